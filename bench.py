@@ -1,0 +1,552 @@
+"""Benchmark: exact edit distance (Landau-Vishkin BFS) on one GB300.
+
+Default workload (one "step"): the three n = 10^8, alphabet-4 pairs with
+k = 10, 10^3, 10^5 planted edits, each solved by one persistent launch of
+the single-pair kernel.  Metric: diagonal-extensions per second (one
+extension = one (round, diagonal) cell of Algorithm 1), with compared string
+bytes per second against the measured HBM bandwidth as the roofline.
+
+Other workloads: --workload small (n = 10^6, 100 edits), large (n = 10^9
+Zipf, bursty 10^4 edits), batch (4096 uneven pairs; pairs/s), serve (Poisson
+arrivals, continuous batching; pairs/s and p50/p99 latency).
+
+--impl reference times the CPU oracle (test infrastructure, plain C) on the
+host cores on a bounded sample of the same workload; there is no other
+reference implementation of this method to install.
+
+Multi-GPU: a single pair does not shard (every round needs its neighbours'
+values), so --gpus N runs N replicas (one process per GPU under torchrun);
+value = units processed by all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------------ env
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Dist:
+    def __init__(self):
+        self.ws, self.rank, self.local = dist_env()
+        self.pg = None
+        if self.ws > 1:
+            import torch.distributed as td
+
+            td.init_process_group("gloo")
+            self.pg = td
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([v], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+
+        t = torch.tensor([v], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+class Clocks:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.th:
+            self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_2306_17461_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(name: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(p):
+        return None
+    src, traffic = None, None
+    with open(p) as f:
+        for line in f:
+            if line.startswith("source_hash:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith("traffic_bytes_per_launch:"):
+                traffic = float(line.split(":", 1)[1].strip())
+    if src != src_hash():
+        return None
+    return traffic
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, args):
+    from paper_2306_17461_gb300 import workloads as W
+
+    if name == "mid":
+        ks = [int(x) for x in args.ks.split(",")]
+        pairs = [W.single_mid(k, n=args.n or 10**8) for k in ks]
+        desc = f"single pair, n={args.n or 10**8} sigma=4 uniform, planted k in {ks}, one launch per pair"
+    elif name == "small":
+        pairs = [W.single_small(n=args.n or 10**6)]
+        desc = "single pair, n=1e6 sigma=4 uniform, 100 planted edits"
+    elif name == "large":
+        pairs = [W.single_large(n=args.n or 10**9)]
+        desc = "single pair, n=1e9 Zipf(1.1) over 256 symbols, 1e4 edits in geometric bursts"
+    else:
+        raise ValueError(name)
+    return pairs, desc
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_single(args, D: Dist):
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    pairs, desc = make_workload(args.workload, args)
+    lcp_mode = {"direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH}[args.lcp]
+    ctx = ed.Context(device=D.local, lcp_mode=lcp_mode)
+    dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
+    dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+
+    def step(record=None):
+        for i in range(len(pairs)):
+            k = ed.ed_distance_dev(ctx.h, dA[i], dB[i], stream)
+            if record is not None:
+                st = ed.ed_last_stats(ctx.h)
+                record.append((i, k, st))
+
+    for _ in range(args.warmup):
+        step()
+    recs = []
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(D.local)
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(recs)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    D.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    ext = sum(r[2]["extensions"] for r in recs)
+    cbytes = sum(r[2]["compared_bytes"] for r in recs)
+    kms = sum(r[2]["kernel_ms"] for r in recs)
+    launches = sum(r[2]["kernel_launches"] for r in recs)
+    per = {}
+    for i, k, st in recs:
+        d = per.setdefault(i, {"k": k, "planted": pairs[i].edits, "n": int(pairs[i].A.size),
+                               "ms": [], "ext": st["extensions"], "compared_bytes": st["compared_bytes"],
+                               "long_slides": st["long_slides"], "wide_rounds": st["wide_rounds"]})
+        d["ms"].append(st["kernel_ms"])
+    for d in per.values():
+        d["ms"] = round(statistics.median(d["ms"]), 4)
+        d["ext_per_s"] = d["ext"] / (d["ms"] / 1e3) if d["ms"] else None
+    # e2e: host buffers through ed_distance (H2D inside the timed region)
+    hA = [torch.from_numpy(p.A).pin_memory() for p in pairs]
+    hB = [torch.from_numpy(p.B).pin_memory() for p in pairs]
+    for i in range(len(pairs)):
+        ed.ed_distance(ctx.h, hA[i], hB[i])
+    D.barrier()
+    t0 = time.perf_counter()
+    e_ext = 0
+    for _ in range(args.steps):
+        for i in range(len(pairs)):
+            ed.ed_distance(ctx.h, hA[i], hB[i])
+            e_ext += ed.ed_last_stats(ctx.h)["extensions"]
+    e2e_s = D.max(time.perf_counter() - t0)
+    h2d = sum(int(p.A.size + p.B.size) for p in pairs)
+    ctx.close()
+    secs = D.max(ms / 1e3)
+    ext_all = D.sum(ext)
+    peak, peak_src = peaks()
+    achieved = (cbytes / (kms / 1e3)) / 1e9 if kms else 0.0
+    res = {
+        "metric": "diagonal-extensions/s",
+        "value": ext_all / secs,
+        "unit": "ext/s",
+        "n_gpus": D.ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": desc, "lcp": args.lcp, "pairs_per_step": len(pairs),
+                   "l2": "no flush: each pair's strings (>= 2e8 B) exceed the 129 MB L2",
+                   "parallelism": f"replicas x{D.ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                     "kernel": "lv_single_kernel",
+                     "traffic": profile_traffic(f"lv_single_{args.workload}.md"),
+                     "algorithmic_bytes_per_launch": cbytes / max(1, len(recs))},
+        "e2e": {"value": D.sum(e_ext) / e2e_s, "unit": "ext/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": 8 * len(pairs) * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "per_pair": per,
+    }
+    return res, pairs
+
+
+def run_batch(args, D: Dist):
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+    from paper_2306_17461_gb300 import workloads as W
+
+    torch.cuda.set_device(D.local)
+    dev = torch.device("cuda", D.local)
+    npairs = args.npairs
+    shapes = W.batch_shapes(npairs)
+    mine = list(range(D.rank, npairs, D.ws))  # pairs sharded round-robin over ranks
+    pairs = [W.make_pair(4, int(shapes[0][p]), int(shapes[1][p]), sigma=int(shapes[2][p]), extra=p + 1)
+             for p in mine]
+    ctx = ed.Context(device=D.local)
+    dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
+    dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        ed.ed_distance_batch_dev(ctx.h, dA, dB)
+    D.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(D.local)
+    clocks.start()
+    t0 = time.perf_counter()
+    ext = launches = 0
+    for _ in range(args.steps):
+        ed.ed_distance_batch_dev(ctx.h, dA, dB)
+        st = ed.ed_last_stats(ctx.h)
+        ext += st["extensions"]
+        launches += st["kernel_launches"]
+    torch.cuda.synchronize()
+    secs = D.max(time.perf_counter() - t0)
+    clk = clocks.stop()
+    # one-pair-at-a-time baseline on the same pairs (single-pair kernel)
+    t1 = time.perf_counter()
+    for i in range(len(pairs)):
+        ed.ed_distance_dev(ctx.h, dA[i], dB[i])
+    torch.cuda.synchronize()
+    one_s = D.max(time.perf_counter() - t1)
+    ctx.close()
+    total_pairs = npairs * args.steps
+    res = {
+        "metric": "batched pairs/s",
+        "value": total_pairs / secs,
+        "unit": "pairs/s",
+        "n_gpus": D.ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": secs * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "strong",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"{npairs} pairs, n log-uniform [1e3,1e6], sigma 4/64, edit rate log-uniform [1e-4,5e-2]",
+                   "parallelism": f"pairs sharded over {D.ws} GPUs"},
+        "ext_per_s": D.sum(ext) / secs,
+        "one_at_a_time_pairs_per_s": npairs / one_s,
+        "speedup_vs_one_at_a_time": (total_pairs / secs) / (npairs / one_s),
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return res, None
+
+
+def run_serve(args, D: Dist):
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+    from paper_2306_17461_gb300 import workloads as W
+
+    torch.cuda.set_device(D.local)
+    pairs = W.serve_pairs(args.npairs_serve)
+    rates = [float(r) for r in args.rates.split(",")]
+    ctx = ed.Context(device=D.local, max_inflight=1024)
+    # warm-up
+    for p in pairs[:8]:
+        t = ed.ed_submit(ctx.h, p.A, p.B)
+        while ed.ed_poll(ctx.h, t)[0] != ed.ED_OK:
+            time.sleep(0.0005)
+    out = []
+    for ri, rate in enumerate(rates):
+        arr = W.poisson_arrivals(rate, len(pairs), seed_extra=ri)
+        lat = [None] * len(pairs)
+        sub_t = [None] * len(pairs)
+        tickets = {}
+        t0 = time.perf_counter()
+        i = 0
+        while i < len(pairs) or tickets:
+            now = time.perf_counter() - t0
+            while i < len(pairs) and arr[i] <= now:
+                try:
+                    tickets[ed.ed_submit(ctx.h, pairs[i].A, pairs[i].B)] = i
+                    sub_t[i] = arr[i]
+                    i += 1
+                except ed.EdError as e:
+                    if e.code != ed.ED_EBUSY:
+                        raise
+                    break
+            for t in list(tickets):
+                st, k = ed.ed_poll(ctx.h, t)
+                if st == ed.ED_OK:
+                    j = tickets.pop(t)
+                    lat[j] = (time.perf_counter() - t0) - arr[j]
+            time.sleep(0.0002)
+        span = time.perf_counter() - t0
+        L = np.array(lat) * 1e3
+        out.append({"rate_req_s": rate, "pairs_per_s": len(pairs) / span,
+                    "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
+                    "span_s": span})
+        log(f"serve rate {rate}: {out[-1]}")
+    cnt = ed.ed_serve_counters(ctx.h)
+    ctx.close()
+    best = max(out, key=lambda r: r["pairs_per_s"])
+    res = {
+        "metric": "served pairs/s",
+        "value": best["pairs_per_s"],
+        "unit": "pairs/s",
+        "n_gpus": D.ws,
+        "steps": len(rates),
+        "warmup": 8,
+        "ms_per_step": best["span_s"] * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"{len(pairs)} pairs, n log-uniform [1e2,1e7], edit rate log-uniform [1e-3,1e-1], Poisson arrivals",
+                   "rates": rates},
+        "sweep": out,
+        "p50_ms": best["p50_ms"],
+        "p99_ms": best["p99_ms"],
+        "engine_steps": cnt["steps"],
+    }
+    return res, None
+
+
+# ------------------------------------------------------------------ CPU (oracle)
+def cpu_sample(pairs, budget_s: float):
+    """The oracle (Algorithm 1, char-by-char LCP; OpenMP over the diagonals of
+    a round) on the host cores, on a bounded sample of the workload: each
+    pair runs whole if it fits the time left, else for a number of rounds
+    sized to the budget.  Returns (ext/s, cores, description)."""
+    import oracle
+
+    cores = os.cpu_count() or 1
+    ext_total, t_total, parts = 0, 0.0, []
+    share = budget_s / max(1, len(pairs))
+    for p in pairs:
+        rounds = 64
+        while True:
+            t0 = time.perf_counter()
+            k, r, ext = oracle.lv(p.A, p.B, max_rounds=rounds, nthreads=cores, with_stats=True)
+            dt = time.perf_counter() - t0
+            if k >= 0 or dt > share / 4:
+                break
+            rounds *= 2
+        ext_total += ext
+        t_total += dt
+        parts.append(f"n={p.A.size}: {r} rounds{' (whole pair)' if k >= 0 else ''}")
+    return ext_total / t_total, cores, "; ".join(parts), t_total
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def run_reference(args, D: Dist):
+    if D.rank != 0:
+        return None
+    pairs, desc = make_workload(args.workload if args.workload in ("mid", "small", "large") else "mid", args)
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample(pairs[:1], 1.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, cores, sample, _ = cpu_sample(pairs, args.cpu_budget / max(1, args.steps))
+        vals.append(v)
+    span = time.perf_counter() - t0
+    v = statistics.median(vals)
+    return {
+        "metric": "diagonal-extensions/s",
+        "value": v,
+        "unit": "ext/s",
+        "n_gpus": D.ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": span * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": desc, "lcp": "direct (char by char)"},
+        "cpu_baseline": {"value": v, "unit": "ext/s", "cores": cores, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_model()},
+        "e2e": {"value": v, "unit": "ext/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "small", "large", "batch", "serve"])
+    ap.add_argument("--lcp", default="direct", choices=["direct", "hash"])
+    ap.add_argument("--ks", default="10,1000,100000")
+    ap.add_argument("--n", type=int, default=0)
+    ap.add_argument("--npairs", type=int, default=4096)
+    ap.add_argument("--npairs-serve", type=int, default=512)
+    ap.add_argument("--rates", default="2,5,10,20")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    D = Dist()
+    try:
+        if args.impl == "reference":
+            res = run_reference(args, D)
+            if res is not None:
+                print(json.dumps(res), flush=True)
+            return
+        if args.workload == "batch":
+            res, pairs = run_batch(args, D)
+        elif args.workload == "serve":
+            res, pairs = run_serve(args, D)
+        else:
+            res, pairs = run_single(args, D)
+            if D.rank == 0 and not args.no_cpu_baseline:
+                v, cores, sample, secs = cpu_sample(pairs, args.cpu_budget)
+                res["cpu_baseline"] = {"value": v, "unit": "ext/s", "cores": cores, "kind": "oracle",
+                                       "sample": sample, "seconds": secs, "cpu": cpu_model()}
+        if D.rank == 0:
+            print(json.dumps(res), flush=True)
+    finally:
+        D.close()
+
+
+if __name__ == "__main__":
+    main()

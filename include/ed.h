@@ -1,0 +1,178 @@
+/*
+ * ed.h -- C ABI of the GB300 edit-distance library (libedgb300.so).
+ *
+ * The library computes the exact Levenshtein distance (unit-cost insertion,
+ * deletion and substitution; Sec. 1 and Sec. 2 of "Efficient Parallel
+ * Output-Sensitive Edit Distance") of byte strings with the breadth-first
+ * Landau-Vishkin method of Algorithm 1 (Sec. 3.1, Appendix A), on one GPU.
+ *
+ * Conventions used throughout this header:
+ *   - strings are arrays of uint8_t of the given length; any byte value is a
+ *     symbol (NUL included); lengths 0 are legal;
+ *   - a DP cell (x, y) has consumed x bytes of A and y bytes of B;
+ *     diagonal d = y - x; L_t[d] is the largest x on diagonal d reachable
+ *     with t edits (the paper's f_t[i] with i = -d);
+ *   - n and m must each be below 2^31 - 64 (row values are 32-bit);
+ *   - "host pointer" = ordinary process memory (pinned or pageable);
+ *     "device pointer" = memory of the context's CUDA device;
+ *   - every function returns an ed_status; negative values are failures and
+ *     leave the output arguments unspecified;
+ *   - a context is not thread-safe except for ed_submit / ed_poll, which may
+ *     be called from any thread;
+ *   - the caller keeps ownership of every buffer it passes; the library
+ *     keeps no pointer to a caller buffer after the call returns, except
+ *     where stated for *_dev serving calls.
+ */
+#ifndef ED_GB300_H
+#define ED_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ed_ctx ed_ctx; /* opaque; owns device memory, streams, engine */
+
+typedef enum {
+    ED_OK = 0,         /* success */
+    ED_EAGAIN = 1,     /* ed_poll: request still running */
+    ED_EINVAL = -1,    /* bad argument (NULL with length > 0, size limit, ...) */
+    ED_ENOMEM = -2,    /* device or host allocation failed / budget too small */
+    ED_ECUDA = -3,     /* a CUDA runtime call failed (ed_last_cuda_error) */
+    ED_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    ED_EBUSY = -5,     /* admission refused: no free slot or memory; retry */
+    ED_ENOTFOUND = -6, /* unknown or already-collected ticket */
+    ED_ELIMIT = -7     /* distance exceeds the context's frontier capacity */
+} ed_status;
+
+typedef enum {
+    ED_LCP_AUTO = 0,   /* autotuner picks direct or hash per call */
+    ED_LCP_DIRECT = 1, /* 16-byte direct comparison (Sec. 5.1 fast path) */
+    ED_LCP_HASH = 2    /* prefix-hash doubling search, confirmed directly */
+} ed_lcp_mode;
+
+typedef struct {
+    int device;               /* CUDA device ordinal; -1 = current device */
+    size_t mem_budget_bytes;  /* device bytes the context may hold; 0 = 60% of free */
+    int max_inflight;         /* serving slots; 0 = 1024 */
+    int lcp_mode;             /* ed_lcp_mode */
+    uint64_t hash_seed;       /* selects the hash base; 0 = fixed default */
+    uint64_t spin_limit_ns;   /* bound of every device-side wait; 0 = 2e9 */
+    int grid_ctas;            /* CTAs of the single-pair kernel; 0 = all SMs */
+    int narrow_width;         /* band width run by one CTA before the whole
+                                 grid joins; 0 = autotuned */
+    int64_t max_rounds;       /* frontier capacity in rounds; 0 = derived from
+                                 the budget and the string lengths */
+} ed_config;
+
+typedef struct {
+    uint64_t k;              /* the edit distance */
+    uint64_t extensions;     /* diagonal-extensions: (t, d) cells evaluated */
+    uint64_t slide_chars;    /* sum over extensions of the LCP length */
+    uint64_t compared_bytes; /* 2 * (slide_chars + mismatching compares) */
+    uint64_t long_slides;    /* slides spread over the whole grid */
+    uint64_t wide_rounds;    /* rounds run by the whole grid */
+    uint64_t hash_queries;   /* LCP queries answered by the hash search */
+    uint64_t hash_collisions;/* hash answers refuted by the direct check */
+    uint64_t kernel_launches;/* kernels launched by this call */
+    double kernel_ms;        /* device time of the distance kernel(s) */
+    double build_ms;         /* device time of the prefix-hash build */
+} ed_stats;
+
+/* Fills *cfg with the defaults described in ed_config. */
+int ed_config_default(ed_config *cfg);
+
+/* Creates a context on cfg->device (cfg may be NULL for defaults).  Sizes
+ * its memory pool lazily inside the budget.  *out receives the context. */
+int ed_create(ed_ctx **out, const ed_config *cfg);
+
+/* Waits for or cancels in-flight serving work, frees everything. */
+int ed_destroy(ed_ctx *ctx);
+
+/* Static description of a status code (never NULL). */
+const char *ed_strerror(int status);
+
+/* Text of the last CUDA error seen by the context ("" if none). */
+const char *ed_last_cuda_error(ed_ctx *ctx);
+
+/* Exact distance of one pair; A and B are HOST pointers.  Copies the
+ * strings to the device (inside the call), runs Algorithm 1 in one
+ * persistent kernel launch and returns when *k is known.  Synchronous. */
+int ed_distance(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
+                size_t m, uint64_t *k);
+
+/* As ed_distance, but A and B are DEVICE pointers (any alignment) and the
+ * work is ordered on `stream` (a cudaStream_t; NULL = legacy default).
+ * Returns after the stream reaches the end of the work. */
+int ed_distance_dev(ed_ctx *ctx, const uint8_t *A, size_t n,
+                    const uint8_t *B, size_t m, uint64_t *k, void *stream);
+
+/* Counters of the last ed_distance / ed_distance_dev / batch call. */
+int ed_last_stats(ed_ctx *ctx, ed_stats *out);
+
+/* Many independent pairs (Sec. 6 workloads, batched): A[p], B[p] are
+ * DEVICE pointers of lengths n[p], m[p] (the pointer arrays themselves are
+ * host arrays); k_out is a host array of npairs entries.  One persistent
+ * launch claims pairs from a cost-ordered work queue; pairs whose band
+ * outgrows one CTA continue on the single-pair kernel.  Synchronous. */
+int ed_distance_batch_dev(ed_ctx *ctx, size_t npairs,
+                          const uint8_t *const *A, const size_t *n,
+                          const uint8_t *const *B, const size_t *m,
+                          uint64_t *k_out, void *stream);
+
+/* As ed_distance_batch_dev with HOST string pointers (copied inside). */
+int ed_distance_batch(ed_ctx *ctx, size_t npairs, const uint8_t *const *A,
+                      const size_t *n, const uint8_t *const *B,
+                      const size_t *m, uint64_t *k_out);
+
+/* Serving (continuous batching).  ed_submit copies the HOST strings into
+ * device memory before it returns (the caller may free them at once),
+ * admits the pair when a slot and its memory fit the budget, and returns a
+ * ticket; ED_EBUSY means "not admitted, retry later".  Admitted pairs run
+ * concurrently on the device, each keeping its frontier resident in device
+ * memory between engine steps; pairs retire as soon as they finish.
+ * ed_poll returns ED_OK with *k once the pair is done (the ticket is then
+ * released), ED_EAGAIN while it runs, ED_ENOTFOUND for unknown tickets. */
+int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
+              size_t m, uint64_t *ticket);
+int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k);
+
+/* Serving counters: admitted, completed, in flight, engine steps. */
+int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed,
+                      uint64_t *inflight, uint64_t *steps);
+
+/* ---- building blocks, exported for tests and diagnostics ---------------- */
+
+/* LCP(A, B, x[i], y[i]) of Sec. 2 for q queries; A, B device pointers;
+ * x, y, out host arrays.  method: 0 = per-thread 16-byte compare, 1 = one
+ * warp per query (ballot / first-set-bit), 2 = whole-grid search,
+ * 3 = hash search (needs ed_prefix_hash tables TA, TB as device pointers of
+ * n+1 and m+1 entries; confirmed directly).  Synchronous. */
+int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
+               size_t m, const int64_t *x, const int64_t *y, size_t q,
+               int method, const uint64_t *TA, const uint64_t *TB,
+               int64_t *out, void *stream);
+
+/* The prefix table of Sec. 3.2: T[i] = sum_{j<i} (X[j]+1) * p^(i-1-j)
+ * mod 2^61-1 for i = 0..len, p = ed_hash_base(ctx).  X and T are device
+ * pointers; T has len + 1 uint64 entries.  One single-pass scan launch. */
+int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T,
+                       void *stream);
+
+/* The hash base p used by the context (derived from hash_seed). */
+uint64_t ed_hash_base(ed_ctx *ctx);
+
+/* Runs Algorithm 1 on DEVICE strings for rounds 0..t_max and writes the
+ * frontiers to the HOST array out[t * (2*t_max+1) + (d + t_max)] (int32;
+ * INT32 value -1061109568 where undefined).  *k receives the distance if
+ * it is <= t_max, else UINT64_MAX.  For parity checks on small inputs. */
+int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n,
+                     const uint8_t *B, size_t m, int64_t t_max, int32_t *out,
+                     uint64_t *k, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ED_GB300_H */

@@ -1,0 +1,993 @@
+// ed_api.cu -- host runtime and C ABI of libedgb300 (declared in include/ed.h).
+//
+// The context owns: one CUDA stream, a pool of device buffers grown on demand
+// inside the memory budget, the pinned result block, and (when serving is
+// used) a continuous-batching engine thread with a device arena.  Every
+// compute step runs in the kernels of lv_single.cu, lv_batch.cu and hash.cu;
+// this file only validates, plans, allocates and launches.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <numeric>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ed.h"
+#include "lv_kernels.cuh"
+
+using namespace edg;
+
+namespace {
+
+constexpr int64_t MAX_LEN = (1ll << 31) - 64;
+constexpr uint64_t Q61H = (1ull << 61) - 1;
+
+// host mod 2^61-1 (exact 128-bit product)
+uint64_t hmul(uint64_t a, uint64_t b)
+{
+    const unsigned __int128 p = (unsigned __int128)a * b;
+    uint64_t r = (uint64_t)(p & Q61H) + (uint64_t)(p >> 61);
+    r = (r & Q61H) + (r >> 61);
+    return r >= Q61H ? r - Q61H : r;
+}
+
+uint64_t splitmix(uint64_t x)
+{
+    x += 0x9e3779b97f4a7c15ull;
+    x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ull;
+    x = (x ^ (x >> 27)) * 0x94d049bb133111ebull;
+    return x ^ (x >> 31);
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// First-fit arena over one device allocation (serving strings and frontiers).
+struct Arena {
+    char *base = nullptr;
+    size_t size = 0;
+    std::map<size_t, size_t> free_; // offset -> length
+    std::mutex mu;
+    void init(char *b, size_t s)
+    {
+        base = b;
+        size = s;
+        free_.clear();
+        free_[0] = s;
+    }
+    char *alloc(size_t n)
+    {
+        n = (n + 255) & ~(size_t)255;
+        std::lock_guard<std::mutex> g(mu);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const size_t off = it->first, len = it->second;
+                free_.erase(it);
+                if (len > n)
+                    free_[off + n] = len - n;
+                return base + off;
+            }
+        }
+        return nullptr;
+    }
+    void release(char *p, size_t n)
+    {
+        if (!p)
+            return;
+        n = (n + 255) & ~(size_t)255;
+        std::lock_guard<std::mutex> g(mu);
+        size_t off = (size_t)(p - base);
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + n == nx->first) {
+            n += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+};
+
+struct Request {
+    uint64_t ticket;
+    char *dA = nullptr, *dB = nullptr, *front = nullptr;
+    size_t bytesA = 0, bytesB = 0, bytesF = 0;
+    int64_t n = 0, m = 0;
+    int32_t t = -1;
+    int32_t state = 0;
+    int64_t k = -1;
+};
+
+} // namespace
+
+struct ed_ctx {
+    ed_config cfg{};
+    int device = 0;
+    int num_sms = 0;
+    int coop_grid = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_err;
+    size_t budget = 0;
+    size_t held = 0;
+    // pool
+    DevBuf strA, strB, gf0, gf1, job, items, res, dump, hashA, hashB, scan, qx, qy, qo, bpairs, border,
+        bnext, bfront;
+    unsigned long long *h_res = nullptr; // pinned
+    uint64_t hash_base = 0;
+    HashArgs hash{};
+    ed_stats last{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
+    std::mutex api_mu; // serialises the synchronous calls against the engine
+    // serving
+    std::thread engine;
+    std::mutex smu;
+    std::condition_variable scv;
+    bool stop = false;
+    bool engine_on = false;
+    Arena arena;
+    DevBuf arena_buf;
+    std::deque<Request *> pending;
+    std::vector<Request *> live;
+    std::map<uint64_t, int64_t> results; // ticket -> k (or negative status)
+    std::map<uint64_t, bool> known;
+    uint64_t next_ticket = 1;
+    uint64_t n_admitted = 0, n_completed = 0, n_steps = 0;
+    cudaStream_t sstream = nullptr, cstream = nullptr;
+    DevBuf s_pairs, s_order, s_next;
+};
+
+namespace {
+
+int cuda_fail(ed_ctx *c, cudaError_t e, const char *what)
+{
+    if (c) {
+        c->last_err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return ED_ECUDA;
+}
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess)                                                                     \
+            return cuda_fail(ctx, e_, #call);                                                      \
+    } while (0)
+
+int ensure(ed_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (b.bytes >= bytes)
+        return ED_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->held -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = std::max(bytes, (size_t)4096);
+    if (ctx->held + want > ctx->budget)
+        return ED_ENOMEM;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        cudaGetLastError();
+        ctx->last_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return ED_ENOMEM;
+    }
+    b.bytes = want;
+    ctx->held += want;
+    return ED_OK;
+}
+
+void release(ed_ctx *ctx, DevBuf &b)
+{
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->held -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int status_from_kernel(unsigned long long st)
+{
+    if (st == 0)
+        return ED_OK;
+    if (st == ST_TIMEOUT)
+        return ED_ETIMEOUT;
+    if (st == ST_LIMIT)
+        return ED_ELIMIT;
+    return ED_ECUDA;
+}
+
+uint64_t count_extensions(int64_t n, int64_t m, int64_t k)
+{
+    // sum over t = 0..k of the diagonals of [-t, t] inside [-n, m]
+    uint64_t e = 0;
+    auto S = [](int64_t a, int64_t b) -> uint64_t { // sum_{t=0}^{b} min(t, a)
+        if (b < 0)
+            return 0;
+        if (b <= a)
+            return (uint64_t)b * (uint64_t)(b + 1) / 2;
+        return (uint64_t)a * (uint64_t)(a + 1) / 2 + (uint64_t)(b - a) * (uint64_t)a;
+    };
+    e = (uint64_t)(k + 1) + S(n, k) + S(m, k);
+    return e;
+}
+
+// Plan of one single-pair launch.
+struct Plan {
+    int W0, grid, t1, t2, use_hash;
+};
+
+Plan plan_pair(ed_ctx *ctx, int64_t n, int64_t m)
+{
+    Plan p;
+    p.W0 = ctx->cfg.narrow_width > 0 ? (ctx->cfg.narrow_width & ~1) : 2048;
+    p.grid = ctx->coop_grid;
+    p.t1 = 64;
+    p.t2 = 8192;
+    p.use_hash = ctx->cfg.lcp_mode == ED_LCP_HASH;
+    (void)n;
+    (void)m;
+    return p;
+}
+
+int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
+                    cudaStream_t s)
+{
+    int r;
+    if ((r = ensure(ctx, ctx->hashA, sizeof(uint64_t) * (n + 1))) != ED_OK)
+        return r;
+    if ((r = ensure(ctx, ctx->hashB, sizeof(uint64_t) * (m + 1))) != ED_OK)
+        return r;
+    const size_t sb = std::max(prefix_hash_state_bytes(n), prefix_hash_state_bytes(m));
+    if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
+        return r;
+    CK(launch_prefix_hash(dA, n, ctx->hash_base, 0, (uint64_t *)ctx->hashA.p, ctx->scan.p,
+                          prefix_hash_state_bytes(n), s));
+    CK(launch_prefix_hash(dB, m, ctx->hash_base, 0, (uint64_t *)ctx->hashB.p, ctx->scan.p,
+                          prefix_hash_state_bytes(m), s));
+    ctx->last.kernel_launches += 2;
+    return ED_OK;
+}
+
+// One pair, device strings, on stream s.  Fills ctx->last.
+int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
+             cudaStream_t s, int32_t *dump, int64_t dump_tmax, uint64_t *k_out)
+{
+    int r;
+    const Plan pl = plan_pair(ctx, n, m);
+    int64_t kcap = std::max(n, m) + 1;
+    if (ctx->cfg.max_rounds > 0)
+        kcap = std::min<int64_t>(kcap, ctx->cfg.max_rounds);
+    kcap = std::min<int64_t>(kcap, (int64_t)1 << 28);
+    kcap = std::max<int64_t>(kcap, pl.W0 / 2 + 2);
+    const size_t gfb = sizeof(int32_t) * (size_t)(2 * kcap + 5);
+    if ((r = ensure(ctx, ctx->gf0, gfb)) != ED_OK || (r = ensure(ctx, ctx->gf1, gfb)) != ED_OK)
+        return r;
+    if ((r = ensure(ctx, ctx->job, sizeof(LvJob))) != ED_OK)
+        return r;
+    const int item_cap = std::max(pl.W0 + 1, 65536);
+    if ((r = ensure(ctx, ctx->items, sizeof(LongItem) * item_cap)) != ED_OK)
+        return r;
+    if ((r = ensure(ctx, ctx->res, sizeof(unsigned long long) * R_COUNT)) != ED_OK)
+        return r;
+    float build_ms = 0.f;
+    if (pl.use_hash) {
+        CK(cudaEventRecord(ctx->ev2, s));
+        if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
+            return r;
+    }
+    PairArgs P{};
+    P.A = dA;
+    P.B = dB;
+    P.n = n;
+    P.m = m;
+    P.kcap = (int32_t)kcap;
+    P.W0 = pl.W0;
+    P.gf0 = (int32_t *)ctx->gf0.p;
+    P.gf1 = (int32_t *)ctx->gf1.p;
+    P.job = (LvJob *)ctx->job.p;
+    P.items = (LongItem *)ctx->items.p;
+    P.item_cap = item_cap;
+    P.t1_cap = pl.t1;
+    P.t2_cap = pl.t2;
+    P.use_hash = pl.use_hash;
+    if (pl.use_hash) {
+        P.hash = ctx->hash;
+        P.hash.TA = (const uint64_t *)ctx->hashA.p;
+        P.hash.TB = (const uint64_t *)ctx->hashB.p;
+    }
+    P.res = (unsigned long long *)ctx->res.p;
+    P.dump = dump;
+    P.dump_tmax = (int32_t)dump_tmax;
+    P.spin_ns = ctx->cfg.spin_limit_ns;
+    P.idle_ns = std::max<uint64_t>(ctx->cfg.spin_limit_ns * 60, 120000000000ull);
+    CK(cudaMemsetAsync(ctx->job.p, 0, sizeof(LvJob), s));
+    CK(cudaMemsetAsync(ctx->res.p, 0, sizeof(unsigned long long) * R_COUNT, s));
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(launch_lv_single(P, pl.grid, s));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaMemcpyAsync(ctx->h_res, ctx->res.p, sizeof(unsigned long long) * R_COUNT,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->last.kernel_launches += 1;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    if (pl.use_hash)
+        cudaEventElapsedTime(&build_ms, ctx->ev2, ctx->ev0);
+    const unsigned long long *R = ctx->h_res;
+    const int st = status_from_kernel(R[R_STATUS]);
+    if (st != ED_OK)
+        return st;
+    const uint64_t k = R[R_K];
+    ctx->last.k = k;
+    ctx->last.extensions = count_extensions(n, m, (int64_t)k);
+    ctx->last.slide_chars = R[R_SLIDE];
+    ctx->last.compared_bytes = 2ull * (R[R_SLIDE] + R[R_MISMATCH]);
+    ctx->last.long_slides = R[R_LONG];
+    ctx->last.wide_rounds = R[R_WIDE];
+    ctx->last.hash_queries = R[R_HASHQ];
+    ctx->last.hash_collisions = R[R_HASHCOLL];
+    ctx->last.kernel_ms += ms;
+    ctx->last.build_ms += build_ms;
+    *k_out = k;
+    return ED_OK;
+}
+
+bool bad_len(size_t n) { return n > (size_t)MAX_LEN; }
+
+} // namespace
+
+// =====================================================================
+extern "C" {
+
+const char *ed_strerror(int s)
+{
+    switch (s) {
+    case ED_OK: return "ok";
+    case ED_EAGAIN: return "not ready";
+    case ED_EINVAL: return "invalid argument";
+    case ED_ENOMEM: return "out of memory or over the memory budget";
+    case ED_ECUDA: return "CUDA error";
+    case ED_ETIMEOUT: return "a bounded device-side wait timed out";
+    case ED_EBUSY: return "busy: no free slot or memory, retry";
+    case ED_ENOTFOUND: return "unknown ticket";
+    case ED_ELIMIT: return "distance exceeds the frontier capacity";
+    default: return "unknown status";
+    }
+}
+
+int ed_config_default(ed_config *cfg)
+{
+    if (!cfg)
+        return ED_EINVAL;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->device = -1;
+    cfg->mem_budget_bytes = 0;
+    cfg->max_inflight = 1024;
+    cfg->lcp_mode = ED_LCP_AUTO;
+    cfg->hash_seed = 0;
+    cfg->spin_limit_ns = 2000000000ull;
+    cfg->grid_ctas = 0;
+    cfg->narrow_width = 0;
+    cfg->max_rounds = 0;
+    return ED_OK;
+}
+
+const char *ed_last_cuda_error(ed_ctx *ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+int ed_create(ed_ctx **out, const ed_config *cfg)
+{
+    if (!out)
+        return ED_EINVAL;
+    *out = nullptr;
+    std::unique_ptr<ed_ctx> c(new ed_ctx());
+    ed_ctx *ctx = c.get();
+    if (cfg)
+        c->cfg = *cfg;
+    else
+        ed_config_default(&c->cfg);
+    if (c->cfg.spin_limit_ns == 0)
+        c->cfg.spin_limit_ns = 2000000000ull;
+    if (c->cfg.max_inflight <= 0)
+        c->cfg.max_inflight = 1024;
+    if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 2)
+        return ED_EINVAL;
+    int dev = c->cfg.device;
+    if (dev < 0)
+        CK(cudaGetDevice(&dev));
+    CK(cudaSetDevice(dev));
+    c->device = dev;
+    CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    c->budget = c->cfg.mem_budget_bytes ? c->cfg.mem_budget_bytes : (size_t)(fr * 0.6);
+    // co-resident grid for the cooperative single-pair kernel: one
+    // 1024-thread CTA per SM
+    c->coop_grid = c->cfg.grid_ctas > 0 ? std::min(c->cfg.grid_ctas, c->num_sms) : c->num_sms;
+    c->coop_grid = std::min(c->coop_grid, MAX_GRID);
+    CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&c->ev0));
+    CK(cudaEventCreate(&c->ev1));
+    CK(cudaEventCreate(&c->ev2));
+    CK(cudaMallocHost((void **)&c->h_res, sizeof(unsigned long long) * 64));
+    // hash base: seeded, in [2^8, q-2]
+    const uint64_t seed = c->cfg.hash_seed ? c->cfg.hash_seed : 0x5eed2306174610ull;
+    c->hash_base = 256 + splitmix(seed) % (Q61H - 2 - 256);
+    c->hash.pow2[0] = c->hash_base;
+    for (int j = 1; j < 62; j++)
+        c->hash.pow2[j] = hmul(c->hash.pow2[j - 1], c->hash.pow2[j - 1]);
+    *out = c.release();
+    return ED_OK;
+}
+
+static void engine_stop(ed_ctx *ctx);
+
+int ed_destroy(ed_ctx *ctx)
+{
+    if (!ctx)
+        return ED_EINVAL;
+    engine_stop(ctx);
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf *bufs[] = {&ctx->strA, &ctx->strB, &ctx->gf0,   &ctx->gf1,    &ctx->job,    &ctx->items,
+                      &ctx->res,  &ctx->dump, &ctx->hashA, &ctx->hashB,  &ctx->scan,   &ctx->qx,
+                      &ctx->qy,   &ctx->qo,   &ctx->bpairs, &ctx->border, &ctx->bnext, &ctx->bfront,
+                      &ctx->arena_buf, &ctx->s_pairs, &ctx->s_order, &ctx->s_next};
+    for (DevBuf *b : bufs)
+        release(ctx, *b);
+    if (ctx->h_res)
+        cudaFreeHost(ctx->h_res);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return ED_OK;
+}
+
+uint64_t ed_hash_base(ed_ctx *ctx) { return ctx ? ctx->hash_base : 0; }
+
+int ed_last_stats(ed_ctx *ctx, ed_stats *out)
+{
+    if (!ctx || !out)
+        return ED_EINVAL;
+    *out = ctx->last;
+    return ED_OK;
+}
+
+int ed_distance_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
+                    uint64_t *k, void *stream)
+{
+    if (!ctx || !k || (n && !A) || (m && !B) || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->last = ed_stats{};
+    return run_pair(ctx, A, (int64_t)n, B, (int64_t)m, (cudaStream_t)stream, nullptr, 0, k);
+}
+
+int ed_distance(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, uint64_t *k)
+{
+    if (!ctx || !k || (n && !A) || (m && !B) || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->last = ed_stats{};
+    int r;
+    if ((r = ensure(ctx, ctx->strA, n + 64)) != ED_OK || (r = ensure(ctx, ctx->strB, m + 64)) != ED_OK)
+        return r;
+    if (n)
+        CK(cudaMemcpyAsync(ctx->strA.p, A, n, cudaMemcpyHostToDevice, ctx->stream));
+    if (m)
+        CK(cudaMemcpyAsync(ctx->strB.p, B, m, cudaMemcpyHostToDevice, ctx->stream));
+    return run_pair(ctx, (const uint8_t *)ctx->strA.p, (int64_t)n, (const uint8_t *)ctx->strB.p,
+                    (int64_t)m, ctx->stream, nullptr, 0, k);
+}
+
+int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
+                     int64_t t_max, int32_t *out, uint64_t *k, void *stream)
+{
+    if (!ctx || !k || !out || t_max < 0 || t_max > 4096 || (n && !A) || (m && !B) || bad_len(n) ||
+        bad_len(m))
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->last = ed_stats{};
+    const size_t cnt = (size_t)(t_max + 1) * (size_t)(2 * t_max + 1);
+    int r;
+    if ((r = ensure(ctx, ctx->dump, cnt * sizeof(int32_t))) != ED_OK)
+        return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(ctx->dump.p, 0xC0, cnt * sizeof(int32_t), s));
+    uint64_t kk = 0;
+    r = run_pair(ctx, A, (int64_t)n, B, (int64_t)m, s, (int32_t *)ctx->dump.p, t_max, &kk);
+    if (r != ED_OK)
+        return r;
+    CK(cudaMemcpy(out, ctx->dump.p, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    *k = kk <= (uint64_t)t_max ? kk : UINT64_MAX;
+    return ED_OK;
+}
+
+int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T, void *stream)
+{
+    if (!ctx || !T || (len && !X) || bad_len(len))
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    int r;
+    const size_t sb = prefix_hash_state_bytes((int64_t)len);
+    if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
+        return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, 0, T, ctx->scan.p, sb, s));
+    CK(cudaStreamSynchronize(s));
+    return ED_OK;
+}
+
+int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
+               const int64_t *x, const int64_t *y, size_t q, int method, const uint64_t *TA,
+               const uint64_t *TB, int64_t *out, void *stream)
+{
+    if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 4 || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    if ((method == 3 || method == 4) && (!TA || !TB))
+        return ED_EINVAL;
+    for (size_t i = 0; i < q; i++)
+        if (x[i] < 0 || y[i] < 0 || x[i] > (int64_t)n || y[i] > (int64_t)m)
+            return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    if (q == 0)
+        return ED_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    int r;
+    if (method == 2) {
+        if ((r = ensure(ctx, ctx->items, sizeof(LongItem) * q)) != ED_OK)
+            return r;
+        std::vector<LongItem> it(q);
+        for (size_t i = 0; i < q; i++) {
+            it[i] = LongItem{};
+            it[i].x = x[i];
+            it[i].y = y[i];
+            it[i].lim = std::min<int64_t>((int64_t)n - x[i], (int64_t)m - y[i]);
+            it[i].result = (unsigned long long)it[i].lim;
+        }
+        CK(cudaMemcpyAsync(ctx->items.p, it.data(), sizeof(LongItem) * q, cudaMemcpyHostToDevice, s));
+        CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, nullptr, nullptr, (int64_t)q, 2, nullptr,
+                              nullptr, (LongItem *)ctx->items.p, ctx->coop_grid, s));
+        CK(cudaMemcpyAsync(it.data(), ctx->items.p, sizeof(LongItem) * q, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (size_t i = 0; i < q; i++)
+            out[i] = (int64_t)it[i].result;
+        return ED_OK;
+    }
+    if ((r = ensure(ctx, ctx->qx, 8 * q)) != ED_OK || (r = ensure(ctx, ctx->qy, 8 * q)) != ED_OK ||
+        (r = ensure(ctx, ctx->qo, 8 * q)) != ED_OK)
+        return r;
+    CK(cudaMemcpyAsync(ctx->qx.p, x, 8 * q, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->qy.p, y, 8 * q, cudaMemcpyHostToDevice, s));
+    HashArgs H = ctx->hash;
+    H.TA = TA;
+    H.TB = TB;
+    CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, (const int64_t *)ctx->qx.p,
+                          (const int64_t *)ctx->qy.p, (int64_t)q, method, &H, (int64_t *)ctx->qo.p,
+                          nullptr, ctx->coop_grid, s));
+    CK(cudaMemcpyAsync(out, ctx->qo.p, 8 * q, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ED_OK;
+}
+
+// ------------------------------------------------------------------ batch
+static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const size_t *n,
+                      const uint8_t *const *B, const size_t *m, uint64_t *k_out, cudaStream_t s)
+{
+    int r;
+    const int W = 4096;
+    const size_t fb = sizeof(int32_t) * (W + 3);
+    if ((r = ensure(ctx, ctx->bpairs, sizeof(BatchPair) * np)) != ED_OK ||
+        (r = ensure(ctx, ctx->border, sizeof(int32_t) * np)) != ED_OK ||
+        (r = ensure(ctx, ctx->bnext, 64)) != ED_OK || (r = ensure(ctx, ctx->bfront, fb * np)) != ED_OK)
+        return r;
+    std::vector<BatchPair> hp(np);
+    std::vector<int32_t> order(np);
+    for (size_t p = 0; p < np; p++) {
+        BatchPair &b = hp[p];
+        b = BatchPair{};
+        b.A = A[p];
+        b.B = B[p];
+        b.n = (int64_t)n[p];
+        b.m = (int64_t)m[p];
+        b.front = (int32_t *)((char *)ctx->bfront.p + fb * p);
+        b.t = -1;
+        b.state = 0;
+        b.k = -1;
+        order[p] = (int32_t)p;
+    }
+    // longest-processing-time first: longer pairs are claimed first
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return std::max(n[a], m[a]) > std::max(n[b], m[b]);
+    });
+    CK(cudaMemcpyAsync(ctx->bpairs.p, hp.data(), sizeof(BatchPair) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->border.p, order.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->bnext.p, 0, 64, s));
+    BatchArgs Bg{};
+    Bg.pairs = (BatchPair *)ctx->bpairs.p;
+    Bg.order = (const int32_t *)ctx->border.p;
+    Bg.npairs = (int32_t)np;
+    Bg.W = W;
+    Bg.round_budget = 0;
+    Bg.next = (uint32_t *)ctx->bnext.p;
+    Bg.t1_cap = 64;
+    Bg.t2_cap = 8192;
+    Bg.spin_ns = ctx->cfg.spin_limit_ns;
+    int occ = 0;
+    const size_t smem = lv_batch_smem_bytes(W);
+    // occupancy-sized persistent grid
+    occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+    occ = std::min(occ, 2048 / lv_batch_threads());
+    const int grid = ctx->num_sms * occ;
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(launch_lv_batch(Bg, grid, s, 0));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaMemcpyAsync(hp.data(), ctx->bpairs.p, sizeof(BatchPair) * np, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->last.kernel_launches += 1;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->last.kernel_ms += ms;
+    uint64_t ext = 0, slide = 0, mism = 0;
+    for (size_t p = 0; p < np; p++) {
+        const BatchPair &b = hp[p];
+        if (b.state == 1) {
+            k_out[p] = (uint64_t)b.k;
+            ext += count_extensions(b.n, b.m, b.k);
+            slide += b.slide;
+            mism += b.mism;
+        }
+    }
+    ed_stats keep = ctx->last;
+    // pairs whose band outgrew one CTA: the single-pair kernel, one by one
+    for (size_t p = 0; p < np; p++) {
+        if (hp[p].state == 1)
+            continue;
+        uint64_t kk = 0;
+        ctx->last = ed_stats{};
+        r = run_pair(ctx, A[p], (int64_t)n[p], B[p], (int64_t)m[p], s, nullptr, 0, &kk);
+        if (r != ED_OK)
+            return r;
+        k_out[p] = kk;
+        ext += ctx->last.extensions;
+        slide += ctx->last.slide_chars;
+        mism += ctx->last.compared_bytes / 2 - ctx->last.slide_chars;
+        keep.kernel_ms += ctx->last.kernel_ms;
+        keep.kernel_launches += ctx->last.kernel_launches;
+        keep.long_slides += ctx->last.long_slides;
+        keep.wide_rounds += ctx->last.wide_rounds;
+    }
+    ctx->last = keep;
+    ctx->last.extensions = ext;
+    ctx->last.slide_chars = slide;
+    ctx->last.compared_bytes = 2 * (slide + mism);
+    return ED_OK;
+}
+
+int ed_distance_batch_dev(ed_ctx *ctx, size_t np, const uint8_t *const *A, const size_t *n,
+                          const uint8_t *const *B, const size_t *m, uint64_t *k_out, void *stream)
+{
+    if (!ctx || (np && (!A || !B || !n || !m || !k_out)))
+        return ED_EINVAL;
+    for (size_t p = 0; p < np; p++)
+        if ((n[p] && !A[p]) || (m[p] && !B[p]) || bad_len(n[p]) || bad_len(m[p]))
+            return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->last = ed_stats{};
+    if (np == 0)
+        return ED_OK;
+    return batch_core(ctx, np, A, n, B, m, k_out, (cudaStream_t)stream);
+}
+
+int ed_distance_batch(ed_ctx *ctx, size_t np, const uint8_t *const *A, const size_t *n,
+                      const uint8_t *const *B, const size_t *m, uint64_t *k_out)
+{
+    if (!ctx || (np && (!A || !B || !n || !m || !k_out)))
+        return ED_EINVAL;
+    size_t total = 0;
+    for (size_t p = 0; p < np; p++) {
+        if ((n[p] && !A[p]) || (m[p] && !B[p]) || bad_len(n[p]) || bad_len(m[p]))
+            return ED_EINVAL;
+        total += ((n[p] + 15) & ~(size_t)15) + ((m[p] + 15) & ~(size_t)15);
+    }
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    ctx->last = ed_stats{};
+    if (np == 0)
+        return ED_OK;
+    int r;
+    if ((r = ensure(ctx, ctx->strA, total + 64)) != ED_OK)
+        return r;
+    std::vector<const uint8_t *> dA(np), dB(np);
+    size_t off = 0;
+    for (size_t p = 0; p < np; p++) {
+        char *base = (char *)ctx->strA.p;
+        dA[p] = (const uint8_t *)(base + off);
+        if (n[p])
+            CK(cudaMemcpyAsync(base + off, A[p], n[p], cudaMemcpyHostToDevice, ctx->stream));
+        off += (n[p] + 15) & ~(size_t)15;
+        dB[p] = (const uint8_t *)(base + off);
+        if (m[p])
+            CK(cudaMemcpyAsync(base + off, B[p], m[p], cudaMemcpyHostToDevice, ctx->stream));
+        off += (m[p] + 15) & ~(size_t)15;
+    }
+    return batch_core(ctx, np, dA.data(), n, dB.data(), m, k_out, ctx->stream);
+}
+
+// ------------------------------------------------------------------ serving
+static constexpr int SERVE_W = 4096;
+
+static void engine_loop(ed_ctx *ctx)
+{
+    cudaSetDevice(ctx->device);
+    std::vector<BatchPair> hp;
+    std::vector<int32_t> order;
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(ctx->smu);
+            while (!ctx->stop && ctx->pending.empty() && ctx->live.empty())
+                ctx->scv.wait_for(lk, std::chrono::milliseconds(50));
+            if (ctx->stop)
+                break;
+            while (!ctx->pending.empty()) {
+                ctx->live.push_back(ctx->pending.front());
+                ctx->pending.pop_front();
+            }
+        }
+        const size_t L = ctx->live.size();
+        hp.resize(L);
+        order.resize(L);
+        for (size_t i = 0; i < L; i++) {
+            Request *q = ctx->live[i];
+            BatchPair &b = hp[i];
+            b = BatchPair{};
+            b.A = (const uint8_t *)q->dA;
+            b.B = (const uint8_t *)q->dB;
+            b.n = q->n;
+            b.m = q->m;
+            b.front = (int32_t *)q->front;
+            b.t = q->t;
+            b.state = 0;
+            b.k = -1;
+            order[i] = (int32_t)i;
+        }
+        std::unique_lock<std::mutex> api(ctx->api_mu);
+        bool ok = true;
+        ed_ctx *c = ctx;
+        auto chk = [&](cudaError_t e) {
+            if (e != cudaSuccess) {
+                ok = false;
+                c->last_err = cudaGetErrorString(e);
+            }
+        };
+        if (ensure(ctx, ctx->s_pairs, sizeof(BatchPair) * L) != ED_OK ||
+            ensure(ctx, ctx->s_order, sizeof(int32_t) * L) != ED_OK || ensure(ctx, ctx->s_next, 64) != ED_OK)
+            ok = false;
+        if (ok) {
+            chk(cudaMemcpyAsync(ctx->s_pairs.p, hp.data(), sizeof(BatchPair) * L, cudaMemcpyHostToDevice,
+                                ctx->sstream));
+            chk(cudaMemcpyAsync(ctx->s_order.p, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice,
+                                ctx->sstream));
+            chk(cudaMemsetAsync(ctx->s_next.p, 0, 64, ctx->sstream));
+            BatchArgs Bg{};
+            Bg.pairs = (BatchPair *)ctx->s_pairs.p;
+            Bg.order = (const int32_t *)ctx->s_order.p;
+            Bg.npairs = (int32_t)L;
+            Bg.W = SERVE_W;
+            Bg.round_budget = 0;
+            Bg.next = (uint32_t *)ctx->s_next.p;
+            Bg.t1_cap = 64;
+            Bg.t2_cap = 8192;
+            Bg.spin_ns = ctx->cfg.spin_limit_ns;
+            const size_t smem = lv_batch_smem_bytes(SERVE_W);
+            int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+            occ = std::min(occ, 2048 / lv_batch_threads());
+            // a step gives the live pairs about 2 ms of device time; the
+            // claim order rotates so that every pair is reached
+            const int grid = ctx->num_sms * occ;
+            std::rotate(order.begin(), order.begin() + (ctx->n_steps * (uint64_t)grid) % L, order.end());
+            chk(cudaMemcpyAsync(ctx->s_order.p, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice,
+                                ctx->sstream));
+            chk(launch_lv_batch(Bg, grid, ctx->sstream, 2000000ull));
+            chk(cudaMemcpyAsync(hp.data(), ctx->s_pairs.p, sizeof(BatchPair) * L, cudaMemcpyDeviceToHost,
+                                ctx->sstream));
+            chk(cudaStreamSynchronize(ctx->sstream));
+        }
+        ctx->n_steps++;
+        std::vector<Request *> still;
+        for (size_t i = 0; i < L; i++) {
+            Request *q = ctx->live[i];
+            const BatchPair &b = hp[i];
+            int64_t result = ED_ECUDA;
+            bool done = false;
+            if (!ok) {
+                done = true;
+            } else if (b.state == 1) {
+                result = b.k;
+                done = true;
+            } else if (b.state == 2) {
+                uint64_t kk = 0;
+                int r = run_pair(ctx, (const uint8_t *)q->dA, q->n, (const uint8_t *)q->dB, q->m,
+                                 ctx->sstream, nullptr, 0, &kk);
+                result = r == ED_OK ? (int64_t)kk : r;
+                done = true;
+            } else {
+                q->t = b.t;
+            }
+            if (done) {
+                std::lock_guard<std::mutex> lk(ctx->smu);
+                ctx->results[q->ticket] = result;
+                ctx->n_completed++;
+                ctx->arena.release(q->dA, q->bytesA);
+                ctx->arena.release(q->dB, q->bytesB);
+                ctx->arena.release(q->front, q->bytesF);
+                delete q;
+            } else {
+                still.push_back(q);
+            }
+        }
+        api.unlock();
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->live.swap(still);
+    }
+}
+
+static int engine_start(ed_ctx *ctx)
+{
+    if (ctx->engine_on)
+        return ED_OK;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    size_t want = std::min(ctx->budget > ctx->held ? (ctx->budget - ctx->held) / 2 : 0, fr / 2);
+    want = std::max<size_t>(want, 64ull << 20);
+    int r = ensure(ctx, ctx->arena_buf, want);
+    if (r != ED_OK)
+        return r;
+    ctx->arena.init((char *)ctx->arena_buf.p, ctx->arena_buf.bytes);
+    CK(cudaStreamCreateWithFlags(&ctx->sstream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->cstream, cudaStreamNonBlocking));
+    ctx->stop = false;
+    ctx->engine = std::thread(engine_loop, ctx);
+    ctx->engine_on = true;
+    return ED_OK;
+}
+
+static void engine_stop(ed_ctx *ctx)
+{
+    if (!ctx->engine_on)
+        return;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        ctx->stop = true;
+    }
+    ctx->scv.notify_all();
+    ctx->engine.join();
+    ctx->engine_on = false;
+    for (Request *q : ctx->live)
+        delete q;
+    for (Request *q : ctx->pending)
+        delete q;
+    ctx->live.clear();
+    ctx->pending.clear();
+    if (ctx->sstream)
+        cudaStreamDestroy(ctx->sstream);
+    if (ctx->cstream)
+        cudaStreamDestroy(ctx->cstream);
+    ctx->sstream = ctx->cstream = nullptr;
+}
+
+int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, uint64_t *ticket)
+{
+    if (!ctx || !ticket || (n && !A) || (m && !B) || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    int r = engine_start(ctx);
+    if (r != ED_OK)
+        return r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        if (ctx->live.size() + ctx->pending.size() >= (size_t)ctx->cfg.max_inflight)
+            return ED_EBUSY;
+    }
+    Request *q = new Request();
+    q->n = (int64_t)n;
+    q->m = (int64_t)m;
+    q->bytesA = n + 64;
+    q->bytesB = m + 64;
+    q->bytesF = sizeof(int32_t) * (SERVE_W + 3);
+    q->dA = ctx->arena.alloc(q->bytesA);
+    q->dB = q->dA ? ctx->arena.alloc(q->bytesB) : nullptr;
+    q->front = q->dB ? ctx->arena.alloc(q->bytesF) : nullptr;
+    if (!q->front) {
+        ctx->arena.release(q->dA, q->bytesA);
+        ctx->arena.release(q->dB, q->bytesB);
+        delete q;
+        return ED_EBUSY;
+    }
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaSuccess;
+    if (n)
+        e = cudaMemcpyAsync(q->dA, A, n, cudaMemcpyHostToDevice, ctx->cstream);
+    if (e == cudaSuccess && m)
+        e = cudaMemcpyAsync(q->dB, B, m, cudaMemcpyHostToDevice, ctx->cstream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ctx->cstream);
+    if (e != cudaSuccess) {
+        ctx->arena.release(q->dA, q->bytesA);
+        ctx->arena.release(q->dB, q->bytesB);
+        ctx->arena.release(q->front, q->bytesF);
+        delete q;
+        return cuda_fail(ctx, e, "ed_submit copy");
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        q->ticket = ctx->next_ticket++;
+        ctx->known[q->ticket] = true;
+        ctx->pending.push_back(q);
+        ctx->n_admitted++;
+        *ticket = q->ticket;
+    }
+    ctx->scv.notify_all();
+    return ED_OK;
+}
+
+int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k)
+{
+    if (!ctx || !k)
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    auto it = ctx->results.find(ticket);
+    if (it == ctx->results.end()) {
+        if (ctx->known.count(ticket))
+            return ED_EAGAIN;
+        return ED_ENOTFOUND;
+    }
+    const int64_t v = it->second;
+    ctx->results.erase(it);
+    ctx->known.erase(ticket);
+    if (v < 0)
+        return (int)v;
+    *k = (uint64_t)v;
+    return ED_OK;
+}
+
+int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed, uint64_t *inflight,
+                      uint64_t *steps)
+{
+    if (!ctx)
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->smu);
+    if (admitted) *admitted = ctx->n_admitted;
+    if (completed) *completed = ctx->n_completed;
+    if (inflight) *inflight = ctx->live.size() + ctx->pending.size();
+    if (steps) *steps = ctx->n_steps;
+    return ED_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,280 @@
+// ed_device.cuh -- device building blocks shared by the GB300 kernels.
+//
+// Notation (spec convention, mirrored from the paper's i = x - y):
+//   cell (x, y) = x bytes of A and y bytes of B consumed; diagonal d = y - x;
+//   L_t[d] = furthest row x on diagonal d reachable with t edits.
+// LCP(x, y) (Sec. 2) = length of the longest common prefix of A[x..n) and
+// B[y..m).  The slides below compute it by direct comparison in 16-byte
+// windows (the paper's "compare the leading characters first", Sec. 5.1,
+// widened to a 16-byte vector compare).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace edg {
+
+// "Minus infinity" for frontier entries: a byte pattern so that a memset
+// with 0xC0 initialises a buffer, far enough from 0 that +1 stays negative.
+constexpr int32_t NEG = (int32_t)0xC0C0C0C0;
+
+constexpr uint64_t Q61 = (1ull << 61) - 1;
+
+
+// ---------------------------------------------------------------- timing
+__device__ __forceinline__ uint64_t gtimer()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------- memory ordering
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int32_t ld_cg(const int32_t *p) { return __ldcg(p); }
+__device__ __forceinline__ void st_cg(int32_t *p, int32_t v) { __stcg(p, v); }
+__device__ __forceinline__ int64_t ld_vol64(const int64_t *p)
+{
+    return *(const volatile int64_t *)p;
+}
+
+// ------------------------------------------------------- string windows
+// A 16-byte aligned block is loaded only if it overlaps the string
+// [base, base+len): such a block lies in the same page as a valid byte, so
+// the load cannot fault whatever the alignment of base.  Bytes outside the
+// string are garbage and are always masked by the caller's bound.
+__device__ __forceinline__ uint4 ld_blk(const uint8_t *base, int64_t len, uintptr_t blk)
+{
+    const uintptr_t b = (uintptr_t)base;
+    if (blk + 16 > b && blk < b + (uintptr_t)len)
+        return __ldg(reinterpret_cast<const uint4 *>(blk));
+    return make_uint4(0u, 0u, 0u, 0u);
+}
+
+// 16 bytes of the 32-byte concatenation lo|hi starting at byte s (0..15).
+__device__ __forceinline__ uint4 shift_bytes(uint4 lo, uint4 hi, uint32_t s)
+{
+    const uint32_t q = s >> 2, r = (s & 3u) * 8u;
+    const uint32_t w0 = lo.x, w1 = lo.y, w2 = lo.z, w3 = lo.w;
+    const uint32_t w4 = hi.x, w5 = hi.y, w6 = hi.z, w7 = hi.w;
+    const uint32_t a0 = q == 0 ? w0 : q == 1 ? w1 : q == 2 ? w2 : w3;
+    const uint32_t a1 = q == 0 ? w1 : q == 1 ? w2 : q == 2 ? w3 : w4;
+    const uint32_t a2 = q == 0 ? w2 : q == 1 ? w3 : q == 2 ? w4 : w5;
+    const uint32_t a3 = q == 0 ? w3 : q == 1 ? w4 : q == 2 ? w5 : w6;
+    const uint32_t a4 = q == 0 ? w4 : q == 1 ? w5 : q == 2 ? w6 : w7;
+    uint4 o;
+    o.x = __funnelshift_r(a0, a1, r);
+    o.y = __funnelshift_r(a1, a2, r);
+    o.z = __funnelshift_r(a2, a3, r);
+    o.w = __funnelshift_r(a3, a4, r);
+    return o;
+}
+
+// The 16 bytes base[pos .. pos+16) (two aligned loads and a byte shift).
+__device__ __forceinline__ uint4 load16(const uint8_t *base, int64_t len, int64_t pos)
+{
+    const uintptr_t a = (uintptr_t)(base + pos);
+    const uintptr_t al = a & ~(uintptr_t)15;
+    const uint32_t s = (uint32_t)(a & 15);
+    const uint4 lo = ld_blk(base, len, al);
+    if (s == 0)
+        return lo;
+    const uint4 hi = ld_blk(base, len, al + 16);
+    return shift_bytes(lo, hi, s);
+}
+
+// Index of the first differing byte of two 16-byte windows, 16 if equal.
+__device__ __forceinline__ int first_diff16(uint4 a, uint4 b)
+{
+    const uint64_t d0 = ((uint64_t)(a.y ^ b.y) << 32) | (uint64_t)(a.x ^ b.x);
+    const uint64_t d1 = ((uint64_t)(a.w ^ b.w) << 32) | (uint64_t)(a.z ^ b.z);
+    if (d0)
+        return (__ffsll((long long)d0) - 1) >> 3;
+    if (d1)
+        return 8 + ((__ffsll((long long)d1) - 1) >> 3);
+    return 16;
+}
+
+// ------------------------------------------------------- per-thread slide
+// The aligned 4-byte words holding A[x] and B[y], shifted so that byte 0 is
+// A[x] (resp. B[y]).  Requires x < n and y < m: the words then hold a valid
+// byte and cannot fault.  Issued apart from their use so that several
+// diagonals' loads are in flight together.
+__device__ __forceinline__ void word_load(const uint8_t *A, const uint8_t *B, int64_t x, int64_t y,
+                                          uint32_t &wa, uint32_t &wb)
+{
+    const uintptr_t pa = (uintptr_t)(A + x), pb = (uintptr_t)(B + y);
+    wa = __ldg(reinterpret_cast<const uint32_t *>(pa & ~(uintptr_t)3));
+    wb = __ldg(reinterpret_cast<const uint32_t *>(pb & ~(uintptr_t)3));
+}
+
+// LCP from (x, y) up to `lim` bytes (lim <= min(n-x, m-y)), examining at
+// most `cap` bytes, given the words of word_load (unshifted).  Returns the
+// matched length l (l == lim: no mismatch before lim); *open is set when the
+// first `cap` bytes all matched and lim was not reached (the slide must
+// continue elsewhere).  The words decide most slides; then 16-byte windows.
+__device__ __forceinline__ int64_t slide_thread_w(const uint8_t *A, int64_t n, const uint8_t *B,
+                                                  int64_t m, int64_t x, int64_t y, int64_t lim,
+                                                  int64_t cap, uint32_t wa, uint32_t wb, bool *open)
+{
+    *open = false;
+    if (lim <= 0)
+        return 0;
+    const uint32_t sa = (uint32_t)((uintptr_t)(A + x) & 3), sb = (uint32_t)((uintptr_t)(B + y) & 3);
+    wa >>= 8 * sa;
+    wb >>= 8 * sb;
+    int64_t avail = (int64_t)(4 - max(sa, sb));
+    if (avail > lim)
+        avail = lim;
+    const uint32_t mask = avail >= 4 ? 0xffffffffu : ((1u << (8 * avail)) - 1u);
+    const uint32_t dif = (wa ^ wb) & mask;
+    if (dif)
+        return (__ffs((int)dif) - 1) >> 3;
+    int64_t l = avail;
+    const int64_t stop = min(lim, cap);
+    while (l < stop) {
+        const uint4 va = load16(A, n, x + l);
+        const uint4 vb = load16(B, m, y + l);
+        const int f = first_diff16(va, vb);
+        if (f < 16)
+            return min(l + f, lim);
+        l += 16;
+    }
+    if (l >= lim)
+        return lim;
+    *open = true;
+    return l;
+}
+
+__device__ __forceinline__ int64_t slide_thread(const uint8_t *A, int64_t n, const uint8_t *B,
+                                                int64_t m, int64_t x, int64_t y, int64_t lim,
+                                                int64_t cap, bool *open)
+{
+    if (lim <= 0) {
+        *open = false;
+        return 0;
+    }
+    uint32_t wa, wb;
+    word_load(A, B, x, y, wa, wb);
+    return slide_thread_w(A, n, B, m, x, y, lim, cap, wa, wb, open);
+}
+
+// ------------------------------------------------------- per-warp slide
+// All 32 lanes of the calling warp compare 512 consecutive bytes per step
+// (16 per lane), UNROLL steps in flight; __ballot_sync + __ffs pick the
+// first lane holding a mismatch.  Starts at offset l0 (bytes already known
+// equal), up to `lim` bytes from (x, y), examining at most `cap` further
+// bytes.  Must be called by a whole warp with identical arguments.  Returns
+// the matched length from (x, y); *open as for slide_thread.
+template <int UNROLL = 4>
+__device__ __forceinline__ int64_t slide_warp(const uint8_t *A, int64_t n, const uint8_t *B,
+                                              int64_t m, int64_t x, int64_t y, int64_t l0,
+                                              int64_t lim, int64_t cap, bool *open)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t stop = min(lim, l0 + cap);
+    *open = false;
+    for (int64_t base = l0; base < stop; base += 512 * UNROLL) {
+        uint4 va[UNROLL], vb[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            const int64_t o = base + u * 512 + lane * 16;
+            if (o < lim) {
+                va[u] = load16(A, n, x + o);
+                vb[u] = load16(B, m, y + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            const int64_t o = base + u * 512 + lane * 16;
+            int64_t cand = -1;
+            if (o < lim) {
+                const int f = first_diff16(va[u], vb[u]);
+                if (f < 16 || o + 16 >= lim)
+                    cand = min(o + f, lim);
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, cand >= 0);
+            if (bal) {
+                const int src = __ffs((int)bal) - 1;
+                return __shfl_sync(0xffffffffu, cand, src);
+            }
+        }
+    }
+    if (stop >= lim)
+        return lim;
+    *open = true;
+    return stop;
+}
+
+// ------------------------------------------------------- CTA chunk scan
+// The calling CTA compares A[x+off .. x+off+len) with B[y+off ..) and
+// returns the first mismatching offset (>= off), or -1 if all equal.
+// Every thread must call it; s_min is a shared int64 scratch word.
+template <int UNROLL = 4>
+__device__ __forceinline__ int64_t cta_scan(const uint8_t *A, int64_t n, const uint8_t *B,
+                                            int64_t m, int64_t x, int64_t y, int64_t off,
+                                            int64_t len, unsigned long long *s_min)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0)
+        *s_min = ~0ull;
+    __syncthreads();
+    int64_t best = -1;
+    for (int64_t base = 0; base < len && best < 0; base += (int64_t)nt * 16 * UNROLL) {
+        uint4 va[UNROLL], vb[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            const int64_t o = base + ((int64_t)u * nt + tid) * 16;
+            if (o < len) {
+                va[u] = load16(A, n, x + off + o);
+                vb[u] = load16(B, m, y + off + o);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            const int64_t o = base + ((int64_t)u * nt + tid) * 16;
+            if (best < 0 && o < len) {
+                const int f = first_diff16(va[u], vb[u]);
+                if (f < 16 && o + f < len)
+                    best = off + o + f;
+            }
+        }
+    }
+    if (best >= 0)
+        atomicMin(s_min, (unsigned long long)best);
+    __syncthreads();
+    const unsigned long long r = *s_min;
+    __syncthreads();
+    return r == ~0ull ? -1 : (int64_t)r;
+}
+
+// ------------------------------------------------------- mod 2^61 - 1
+// a * b mod q for a, b < q: the 122-bit product hi:lo splits as
+// (hi << 3 | lo >> 61) * 2^61 + (lo & q), and 2^61 = 1 (mod q).
+__device__ __forceinline__ uint64_t mulmod61(uint64_t a, uint64_t b)
+{
+    const uint64_t lo = a * b;
+    const uint64_t hi = __umul64hi(a, b);
+    uint64_t r = (lo & Q61) + ((hi << 3) | (lo >> 61));
+    r = (r & Q61) + (r >> 61);
+    return r >= Q61 ? r - Q61 : r;
+}
+__device__ __forceinline__ uint64_t addmod61(uint64_t a, uint64_t b)
+{
+    const uint64_t r = a + b;
+    return r >= Q61 ? r - Q61 : r;
+}
+__device__ __forceinline__ uint64_t submod61(uint64_t a, uint64_t b)
+{
+    return a >= b ? a - b : a + Q61 - b;
+}
+
+} // namespace edg

@@ -1,0 +1,148 @@
+"""The single-pair path (one persistent launch of Algorithm 1) against the
+oracle: frontiers round by round, distances on random, planted and
+degenerate pairs, every phase of the kernel (narrow CTA, wide grid, long
+slides handed to the grid, hash LCP), host and device entry points.
+Integer results: the tolerance is zero."""
+import numpy as np
+import pytest
+
+from gpu_util import dev, mirror_oracle_frontier
+from paper_2306_17461_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# kernel configurations exercised: default; a tiny narrow band so the whole
+# grid takes over after a few rounds; few CTAs; the hash LCP
+CONFIGS = {
+    "default": {},
+    "wide": {"narrow_width": 8},
+    "wide_g3": {"narrow_width": 4, "grid_ctas": 3},
+    "one_cta": {"grid_ctas": 1},
+    "hash": {"lcp_mode": 2},
+    "hash_wide": {"lcp_mode": 2, "narrow_width": 6},
+}
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_2306_17461_gb300 import binding as ed
+
+    cs = {name: ed.Context(device=0, **cfg) for name, cfg in CONFIGS.items()}
+    yield cs
+    for c in cs.values():
+        c.close()
+
+
+@pytest.mark.parametrize("cfg", list(CONFIGS))
+def test_frontiers_match_oracle(ctxs, orc, cfg):
+    from paper_2306_17461_gb300 import binding as ed
+
+    ctx = ctxs[cfg]
+    rng = np.random.default_rng(21)
+    for trial in range(12):
+        n = int(rng.integers(0, 300))
+        sigma = [2, 4, 256][trial % 3]
+        A, B = W.random_pair(rng, n, int(rng.integers(0, 25)), sigma)
+        k = orc.lv(A, B)
+        T = k + 2
+        kg, F = ed.ed_frontiers_dev(ctx.h, dev(A), dev(B), T)
+        ko, Fo = orc.lv_frontiers(A, B, T)
+        assert kg == ko == k
+        G = mirror_oracle_frontier(Fo, T, orc.NEG, ed.NEG32)
+        assert np.array_equal(F.astype(np.int64), G), (cfg, trial)
+
+
+@pytest.mark.parametrize("cfg", list(CONFIGS))
+def test_random_pairs(ctxs, orc, cfg):
+    ctx = ctxs[cfg]
+    rng = np.random.default_rng(7)
+    for trial in range(25):
+        sigma = [2, 4, 64, 256][trial % 4]
+        n = int(rng.integers(0, 20000))
+        k = int(rng.integers(0, max(1, n // 10) + 1))
+        A, B = W.random_pair(rng, n, k, sigma)
+        assert ctx.distance_dev(dev(A), dev(B)) == orc.lv(A, B), (cfg, trial)
+
+
+@pytest.mark.parametrize("cfg", ["default", "wide", "hash"])
+def test_degenerate_cases(ctxs, orc, cfg):
+    ctx = ctxs[cfg]
+    E = np.zeros(0, np.uint8)
+    cases = [
+        (E, E),
+        (E, np.arange(7, dtype=np.uint8)),
+        (np.arange(9, dtype=np.uint8), E),
+        (np.zeros(1000, np.uint8), np.zeros(1000, np.uint8)),  # identical, all one symbol
+        (np.zeros(1000, np.uint8), np.ones(1000, np.uint8)),   # nothing matches
+        (np.zeros(500, np.uint8), np.zeros(1500, np.uint8)),   # runs of one symbol: long slides everywhere
+        (np.array([0, 0, 1], np.uint8), np.array([0, 1], np.uint8)),  # NUL bytes
+        (np.arange(256, dtype=np.uint8), np.arange(255, -1, -1, dtype=np.uint8)),
+        (np.array([5], np.uint8), np.array([5], np.uint8)),
+        (np.array([5], np.uint8), np.array([6], np.uint8)),
+    ]
+    for A, B in cases:
+        want = orc.dp(A, B) if A.size * B.size <= 4_000_000 else orc.lv(A, B)
+        assert ctx.distance_dev(dev(A), dev(B)) == want
+        assert ctx.distance(A, B) == want
+
+
+def test_unaligned_device_strings(ctxs, orc):
+    ctx = ctxs["default"]
+    p = W.make_pair(31, 100_000, 60, sigma=4)
+    want = orc.lv(p.A, p.B)
+    for oa, ob in [(1, 2), (3, 15), (8, 0), (15, 7)]:
+        bufA = dev(np.concatenate([np.full(oa, 9, np.uint8), p.A]))
+        bufB = dev(np.concatenate([np.full(ob, 9, np.uint8), p.B]))
+        assert ctx.distance_dev(bufA[oa:], bufB[ob:]) == want
+
+
+@pytest.mark.parametrize("cfg", list(CONFIGS))
+def test_long_slides(ctxs, orc, cfg):
+    """Few edits far apart: slides of up to megabytes, which go from one
+    thread to one warp to the whole grid."""
+    ctx = ctxs[cfg]
+    for idx, (n, k) in enumerate([(2_000_000, 1), (2_000_000, 3), (3_000_000, 12), (500_000, 0)]):
+        p = W.make_pair(40 + idx, n, k, sigma=256)
+        want = orc.lv(p.A, p.B)
+        assert ctx.distance_dev(dev(p.A), dev(p.B)) == want, (cfg, n, k)
+        st = ctx.stats()
+        assert st["k"] == want
+        if cfg == "default" and k > 0:
+            assert st["long_slides"] >= 1
+
+
+def test_stats_counters(ctxs, orc):
+    ctx = ctxs["default"]
+    p = W.make_pair(55, 300_000, 400, sigma=4)
+    k, rounds, ext = orc.lv(p.A, p.B, with_stats=True)
+    assert ctx.distance_dev(dev(p.A), dev(p.B)) == k
+    st = ctx.stats()
+    assert st["extensions"] == ext
+    assert st["kernel_launches"] == 1
+    assert st["compared_bytes"] >= 2 * (p.A.size - p.edits)
+
+
+@pytest.mark.parametrize("k", [10, 1000, 10_000])
+def test_mid_workload_reduced(ctxs, orc, k):
+    """The n = 10^8 alphabet-4 workload, reduced to n = 10^7."""
+    p = W.single_mid(k, n=10_000_000)
+    want = orc.lv(p.A, p.B, nthreads=8)
+    for cfg in ["default", "hash"]:
+        assert ctxs[cfg].distance_dev(dev(p.A), dev(p.B)) == want, cfg
+
+
+def test_single_small_full_size(ctxs, orc):
+    """The n = 10^6, 100 planted edits workload at full size."""
+    p = W.single_small()
+    want = orc.lv(p.A, p.B)
+    assert want <= 100
+    for cfg in ["default", "wide", "hash"]:
+        assert ctxs[cfg].distance_dev(dev(p.A), dev(p.B)) == want
+        assert ctxs[cfg].distance(p.A, p.B) == want
+
+
+def test_large_workload_reduced(ctxs, orc):
+    """The Zipf(1.1), bursty workload, reduced to n = 2*10^7, 2000 edits."""
+    p = W.single_large(n=20_000_000, k=2000)
+    want = orc.lv(p.A, p.B, nthreads=8)
+    assert ctxs["default"].distance_dev(dev(p.A), dev(p.B)) == want
