@@ -60,11 +60,13 @@ typedef struct {
     int lcp_mode;             /* ed_lcp_mode */
     uint64_t hash_seed;       /* selects the hash base; 0 = fixed default */
     uint64_t spin_limit_ns;   /* bound of every device-side wait; 0 = 2e9 */
-    int grid_ctas;            /* CTAs of the single-pair kernel; 0 = all SMs */
-    int narrow_width;         /* band width run by one CTA before the whole
-                                 grid joins; 0 = autotuned */
-    int64_t max_rounds;       /* frontier capacity in rounds; 0 = derived from
-                                 the budget and the string lengths */
+    int grid_ctas;            /* CTAs of the tile kernel; 0 = one per SM */
+    int tile_width;           /* diagonals per CTA in the first epoch (the
+                                 tiles double with the band); 0 = 64 */
+    int block_rounds;         /* rounds between neighbour exchanges (1..16);
+                                 0 = 16 */
+    int64_t max_rounds;       /* frontier capacity in rounds; 0 = the larger
+                                 string length (at most 2^28) */
 } ed_config;
 
 typedef struct {
@@ -72,13 +74,17 @@ typedef struct {
     uint64_t extensions;     /* diagonal-extensions: (t, d) cells evaluated */
     uint64_t slide_chars;    /* sum over extensions of the LCP length */
     uint64_t compared_bytes; /* 2 * (slide_chars + mismatching compares) */
-    uint64_t long_slides;    /* slides spread over the whole grid */
-    uint64_t wide_rounds;    /* rounds run by the whole grid */
+    uint64_t long_slides;    /* slides handed to the job slots (helped) */
+    uint64_t wide_rounds;    /* rounds run in temporal blocks */
     uint64_t hash_queries;   /* LCP queries answered by the hash search */
     uint64_t hash_collisions;/* hash answers refuted by the direct check */
     uint64_t kernel_launches;/* kernels launched by this call */
     double kernel_ms;        /* device time of the distance kernel(s) */
     double build_ms;         /* device time of the prefix-hash build */
+    double phase_ms[6];      /* device time by phase, as seen by the first
+                                CTA of the group: rounds, open slides,
+                                neighbour waits (helping included), epoch
+                                changes; [4], [5] unused */
 } ed_stats;
 
 /* Fills *cfg with the defaults described in ed_config. */

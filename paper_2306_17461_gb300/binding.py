@@ -39,7 +39,8 @@ class ed_config(ctypes.Structure):
         ("hash_seed", ctypes.c_uint64),
         ("spin_limit_ns", ctypes.c_uint64),
         ("grid_ctas", ctypes.c_int),
-        ("narrow_width", ctypes.c_int),
+        ("tile_width", ctypes.c_int),
+        ("block_rounds", ctypes.c_int),
         ("max_rounds", ctypes.c_int64),
     ]
 
@@ -57,6 +58,7 @@ class ed_stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_uint64),
         ("kernel_ms", ctypes.c_double),
         ("build_ms", ctypes.c_double),
+        ("phase_ms", ctypes.c_double * 6),
     ]
 
 
@@ -111,7 +113,7 @@ def _strerror(code: int) -> str:
 def _check(ctx, code: int, what: str):
     if code < 0:
         detail = ""
-        if ctx is not None and code == ED_ECUDA:
+        if ctx is not None and code in (ED_ECUDA, ED_ETIMEOUT):
             detail = load().ed_last_cuda_error(ctx).decode()
         raise EdError(code, what, detail)
     return code
@@ -198,7 +200,9 @@ def ed_distance_dev(ctx, A, B, stream=None) -> int:
 def ed_last_stats(ctx) -> dict:
     s = ed_stats()
     _check(ctx, load().ed_last_stats(ctx, ctypes.byref(s)), "ed_last_stats")
-    return {f: getattr(s, f) for f, _ in ed_stats._fields_}
+    d = {f: getattr(s, f) for f, _ in ed_stats._fields_}
+    d["phase_ms"] = list(d["phase_ms"])
+    return d
 
 
 def _ptr_array(ptrs):

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libedgb300.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
-SOURCES = ["ed_api.cu", "lv_single.cu", "lv_batch.cu", "hash.cu"]
+SOURCES = ["ed_api.cu", "lv_tiles.cu", "lv_batch.cu", "hash.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

@@ -1,9 +1,9 @@
 // ed_api.cu -- host runtime and C ABI of libedgb300 (declared in include/ed.h).
 //
 // The context owns: one CUDA stream, a pool of device buffers grown on demand
-// inside the memory budget, the pinned result block, and (when serving is
+// inside the memory budget, a pinned result block, and (when serving is
 // used) a continuous-batching engine thread with a device arena.  Every
-// compute step runs in the kernels of lv_single.cu, lv_batch.cu and hash.cu;
+// compute step runs in the kernels of lv_tiles.cu, lv_batch.cu and hash.cu;
 // this file only validates, plans, allocates and launches.
 #include <algorithm>
 #include <atomic>
@@ -16,7 +16,6 @@
 #include <map>
 #include <memory>
 #include <mutex>
-#include <numeric>
 #include <string>
 #include <thread>
 #include <vector>
@@ -30,8 +29,9 @@ namespace {
 
 constexpr int64_t MAX_LEN = (1ll << 31) - 64;
 constexpr uint64_t Q61H = (1ull << 61) - 1;
+constexpr int BATCH_W = 4096; // band capacity of one batch CTA
 
-// host mod 2^61-1 (exact 128-bit product)
+// host mod 2^61-1 (exact 128-bit product), for the hash base powers
 uint64_t hmul(uint64_t a, uint64_t b)
 {
     const unsigned __int128 p = (unsigned __int128)a * b;
@@ -105,13 +105,20 @@ struct Arena {
 };
 
 struct Request {
-    uint64_t ticket;
+    uint64_t ticket = 0;
     char *dA = nullptr, *dB = nullptr, *front = nullptr;
     size_t bytesA = 0, bytesB = 0, bytesF = 0;
     int64_t n = 0, m = 0;
     int32_t t = -1;
-    int32_t state = 0;
-    int64_t k = -1;
+};
+
+// One pair handed to the tile kernel.
+struct TileJob {
+    const uint8_t *A, *B;
+    int64_t n, m;
+    const uint64_t *TA, *TB;
+    int32_t *dump;
+    int64_t dump_tmax;
 };
 
 } // namespace
@@ -120,20 +127,21 @@ struct ed_ctx {
     ed_config cfg{};
     int device = 0;
     int num_sms = 0;
-    int coop_grid = 0;
+    int grid = 0; // CTAs of the tile kernel
     cudaStream_t stream = nullptr;
     std::string last_err;
     size_t budget = 0;
     size_t held = 0;
     // pool
-    DevBuf strA, strB, gf0, gf1, job, items, res, dump, hashA, hashB, scan, qx, qy, qo, bpairs, border,
-        bnext, bfront;
-    unsigned long long *h_res = nullptr; // pinned
+    DevBuf strA, strB, gf, ctl, gctl, slots, halo, pdesc, res, dump, hashA, hashB, scan, qx, qy, qo, bpairs,
+        border, bnext, bfront;
+    unsigned long long *h_res = nullptr; // pinned result block
+    size_t h_res_cap = 0;
     uint64_t hash_base = 0;
-    HashArgs hash{};
+    uint64_t pow2[62]{};
     ed_stats last{};
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev2 = nullptr;
-    std::mutex api_mu; // serialises the synchronous calls against the engine
+    std::mutex api_mu; // serialises the synchronous calls and the engine's steps
     // serving
     std::thread engine;
     std::mutex smu;
@@ -156,9 +164,8 @@ namespace {
 
 int cuda_fail(ed_ctx *c, cudaError_t e, const char *what)
 {
-    if (c) {
+    if (c)
         c->last_err = std::string(what) + ": " + cudaGetErrorString(e);
-    }
     return ED_ECUDA;
 }
 #define CK(call)                                                                                   \
@@ -178,7 +185,7 @@ int ensure(ed_ctx *ctx, DevBuf &b, size_t bytes)
         b.p = nullptr;
         b.bytes = 0;
     }
-    size_t want = std::max(bytes, (size_t)4096);
+    const size_t want = std::max(bytes, (size_t)4096);
     if (ctx->held + want > ctx->budget)
         return ED_ENOMEM;
     cudaError_t e = cudaMalloc(&b.p, want);
@@ -203,7 +210,7 @@ void release(ed_ctx *ctx, DevBuf &b)
     b.bytes = 0;
 }
 
-int status_from_kernel(unsigned long long st)
+int status_from_kernel(uint32_t st)
 {
     if (st == 0)
         return ED_OK;
@@ -214,10 +221,9 @@ int status_from_kernel(unsigned long long st)
     return ED_ECUDA;
 }
 
+// sum over t = 0..k of the diagonals of [-t, t] inside [-n, m]
 uint64_t count_extensions(int64_t n, int64_t m, int64_t k)
 {
-    // sum over t = 0..k of the diagonals of [-t, t] inside [-n, m]
-    uint64_t e = 0;
     auto S = [](int64_t a, int64_t b) -> uint64_t { // sum_{t=0}^{b} min(t, a)
         if (b < 0)
             return 0;
@@ -225,27 +231,10 @@ uint64_t count_extensions(int64_t n, int64_t m, int64_t k)
             return (uint64_t)b * (uint64_t)(b + 1) / 2;
         return (uint64_t)a * (uint64_t)(a + 1) / 2 + (uint64_t)(b - a) * (uint64_t)a;
     };
-    e = (uint64_t)(k + 1) + S(n, k) + S(m, k);
-    return e;
+    return (uint64_t)(k + 1) + S(n, k) + S(m, k);
 }
 
-// Plan of one single-pair launch.
-struct Plan {
-    int W0, grid, t1, t2, use_hash;
-};
-
-Plan plan_pair(ed_ctx *ctx, int64_t n, int64_t m)
-{
-    Plan p;
-    p.W0 = ctx->cfg.narrow_width > 0 ? (ctx->cfg.narrow_width & ~1) : 2048;
-    p.grid = ctx->coop_grid;
-    p.t1 = 64;
-    p.t2 = 8192;
-    p.use_hash = ctx->cfg.lcp_mode == ED_LCP_HASH;
-    (void)n;
-    (void)m;
-    return p;
-}
+bool bad_len(size_t n) { return n > (size_t)MAX_LEN; }
 
 int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
                     cudaStream_t s)
@@ -258,99 +247,157 @@ int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB
     const size_t sb = std::max(prefix_hash_state_bytes(n), prefix_hash_state_bytes(m));
     if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
         return r;
-    CK(launch_prefix_hash(dA, n, ctx->hash_base, 0, (uint64_t *)ctx->hashA.p, ctx->scan.p,
+    CK(launch_prefix_hash(dA, n, ctx->hash_base, (uint64_t *)ctx->hashA.p, ctx->scan.p,
                           prefix_hash_state_bytes(n), s));
-    CK(launch_prefix_hash(dB, m, ctx->hash_base, 0, (uint64_t *)ctx->hashB.p, ctx->scan.p,
+    CK(launch_prefix_hash(dB, m, ctx->hash_base, (uint64_t *)ctx->hashB.p, ctx->scan.p,
                           prefix_hash_state_bytes(m), s));
     ctx->last.kernel_launches += 2;
     return ED_OK;
 }
 
-// One pair, device strings, on stream s.  Fills ctx->last.
-int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
-             cudaStream_t s, int32_t *dump, int64_t dump_tmax, uint64_t *k_out)
+// Runs pairs on the tile kernel: groups of group_size CTAs claim pairs from
+// a queue.  k[i] receives each distance; per-pair counters are summed into
+// ctx->last.
+int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cudaStream_t s,
+              std::vector<uint64_t> &k)
 {
     int r;
-    const Plan pl = plan_pair(ctx, n, m);
-    int64_t kcap = std::max(n, m) + 1;
+    const int np = (int)jobs.size();
+    const int G = std::max(1, std::min(group_size, ctx->grid));
+    const int ngroups = std::max(1, ctx->grid / G);
+    const int grid = ngroups * G;
+    const int h = ctx->cfg.block_rounds > 0 ? std::min(ctx->cfg.block_rounds, HMAX) : HMAX;
+    const int s0 = ctx->cfg.tile_width > 0 ? ctx->cfg.tile_width : 64;
+    int64_t nm = 0;
+    for (const TileJob &j : jobs)
+        nm = std::max(nm, std::max(j.n, j.m));
+    int64_t kcap = nm + 1;
     if (ctx->cfg.max_rounds > 0)
         kcap = std::min<int64_t>(kcap, ctx->cfg.max_rounds);
     kcap = std::min<int64_t>(kcap, (int64_t)1 << 28);
-    kcap = std::max<int64_t>(kcap, pl.W0 / 2 + 2);
-    const size_t gfb = sizeof(int32_t) * (size_t)(2 * kcap + 5);
-    if ((r = ensure(ctx, ctx->gf0, gfb)) != ED_OK || (r = ensure(ctx, ctx->gf1, gfb)) != ED_OK)
+    kcap = std::max<int64_t>(kcap, h);
+    const int64_t smax = std::max<int64_t>(
+        std::max<int64_t>(h, s0), std::min<int64_t>(SMAX_LIMIT, (2 * std::min(kcap, nm) + 1 + G - 1) / G + 1));
+    const int64_t gstride = 2 * kcap + 5;
+    if ((r = ensure(ctx, ctx->gf, sizeof(int32_t) * (size_t)(2 * gstride) * ngroups)) != ED_OK ||
+        (r = ensure(ctx, ctx->ctl, sizeof(LaunchCtl))) != ED_OK ||
+        (r = ensure(ctx, ctx->gctl, sizeof(GroupCtl) * ngroups)) != ED_OK ||
+        (r = ensure(ctx, ctx->slots, sizeof(JobSlot) * grid)) != ED_OK ||
+        (r = ensure(ctx, ctx->halo, sizeof(int32_t) * (size_t)grid * 4 * HMAX)) != ED_OK ||
+        (r = ensure(ctx, ctx->pdesc, sizeof(PairDesc) * np)) != ED_OK ||
+        (r = ensure(ctx, ctx->res, sizeof(unsigned long long) * R_COUNT * np)) != ED_OK)
         return r;
-    if ((r = ensure(ctx, ctx->job, sizeof(LvJob))) != ED_OK)
-        return r;
-    const int item_cap = std::max(pl.W0 + 1, 65536);
-    if ((r = ensure(ctx, ctx->items, sizeof(LongItem) * item_cap)) != ED_OK)
-        return r;
-    if ((r = ensure(ctx, ctx->res, sizeof(unsigned long long) * R_COUNT)) != ED_OK)
-        return r;
-    float build_ms = 0.f;
-    if (pl.use_hash) {
-        CK(cudaEventRecord(ctx->ev2, s));
-        if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
-            return r;
+    const size_t hres = sizeof(unsigned long long) * R_COUNT * np + 64;
+    if (ctx->h_res_cap < hres) {
+        if (ctx->h_res)
+            cudaFreeHost(ctx->h_res);
+        ctx->h_res = nullptr;
+        ctx->h_res_cap = 0;
+        CK(cudaMallocHost((void **)&ctx->h_res, hres));
+        ctx->h_res_cap = hres;
     }
-    PairArgs P{};
-    P.A = dA;
-    P.B = dB;
-    P.n = n;
-    P.m = m;
+    std::vector<PairDesc> pd(np);
+    for (int i = 0; i < np; i++) {
+        pd[i] = PairDesc{};
+        pd[i].A = jobs[i].A;
+        pd[i].B = jobs[i].B;
+        pd[i].n = jobs[i].n;
+        pd[i].m = jobs[i].m;
+        pd[i].TA = jobs[i].TA;
+        pd[i].TB = jobs[i].TB;
+        pd[i].res = (unsigned long long *)ctx->res.p + (size_t)R_COUNT * i;
+        pd[i].dump = jobs[i].dump;
+        pd[i].dump_tmax = (int32_t)jobs[i].dump_tmax;
+    }
+    LvArgs P{};
+    P.pairs = (const PairDesc *)ctx->pdesc.p;
+    P.npairs = np;
+    P.group_size = G;
+    P.gctl = (GroupCtl *)ctx->gctl.p;
+    P.ctl = (LaunchCtl *)ctx->ctl.p;
+    P.slots = (JobSlot *)ctx->slots.p;
+    P.halo = (int32_t *)ctx->halo.p;
+    P.gf = (int32_t *)ctx->gf.p;
+    P.gf_stride = 2 * gstride;
     P.kcap = (int32_t)kcap;
-    P.W0 = pl.W0;
-    P.gf0 = (int32_t *)ctx->gf0.p;
-    P.gf1 = (int32_t *)ctx->gf1.p;
-    P.job = (LvJob *)ctx->job.p;
-    P.items = (LongItem *)ctx->items.p;
-    P.item_cap = item_cap;
-    P.t1_cap = pl.t1;
-    P.t2_cap = pl.t2;
-    P.use_hash = pl.use_hash;
-    if (pl.use_hash) {
-        P.hash = ctx->hash;
-        P.hash.TA = (const uint64_t *)ctx->hashA.p;
-        P.hash.TB = (const uint64_t *)ctx->hashB.p;
-    }
-    P.res = (unsigned long long *)ctx->res.p;
-    P.dump = dump;
-    P.dump_tmax = (int32_t)dump_tmax;
+    P.smax = (int32_t)smax;
+    P.h = h;
+    P.s0 = s0;
+    P.t1_cap = 64;
+    P.t2_cap = 2048;
+    P.use_hash = jobs[0].TA != nullptr;
+    std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
     P.spin_ns = ctx->cfg.spin_limit_ns;
-    P.idle_ns = std::max<uint64_t>(ctx->cfg.spin_limit_ns * 60, 120000000000ull);
-    CK(cudaMemsetAsync(ctx->job.p, 0, sizeof(LvJob), s));
-    CK(cudaMemsetAsync(ctx->res.p, 0, sizeof(unsigned long long) * R_COUNT, s));
+    P.idle_ns = ctx->cfg.spin_limit_ns * 60;
+    CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(ctx->ctl.p, 0, sizeof(LaunchCtl), s));
+    CK(cudaMemsetAsync(ctx->gctl.p, 0, sizeof(GroupCtl) * ngroups, s));
+    CK(cudaMemsetAsync(ctx->slots.p, 0, sizeof(JobSlot) * grid, s));
+    CK(cudaMemsetAsync(ctx->res.p, 0, sizeof(unsigned long long) * R_COUNT * np, s));
     CK(cudaEventRecord(ctx->ev0, s));
-    CK(launch_lv_single(P, pl.grid, s));
+    CK(launch_lv_tiles(P, grid, s));
     CK(cudaEventRecord(ctx->ev1, s));
-    CK(cudaMemcpyAsync(ctx->h_res, ctx->res.p, sizeof(unsigned long long) * R_COUNT,
+    CK(cudaMemcpyAsync(ctx->h_res, ctx->res.p, sizeof(unsigned long long) * R_COUNT * np,
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(ctx->h_res + (size_t)R_COUNT * np, ctx->ctl.p, sizeof(uint32_t),
                        cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     ctx->last.kernel_launches += 1;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    if (pl.use_hash)
-        cudaEventElapsedTime(&build_ms, ctx->ev2, ctx->ev0);
-    const unsigned long long *R = ctx->h_res;
-    const int st = status_from_kernel(R[R_STATUS]);
-    if (st != ED_OK)
-        return st;
-    const uint64_t k = R[R_K];
-    ctx->last.k = k;
-    ctx->last.extensions = count_extensions(n, m, (int64_t)k);
-    ctx->last.slide_chars = R[R_SLIDE];
-    ctx->last.compared_bytes = 2ull * (R[R_SLIDE] + R[R_MISMATCH]);
-    ctx->last.long_slides = R[R_LONG];
-    ctx->last.wide_rounds = R[R_WIDE];
-    ctx->last.hash_queries = R[R_HASHQ];
-    ctx->last.hash_collisions = R[R_HASHCOLL];
     ctx->last.kernel_ms += ms;
-    ctx->last.build_ms += build_ms;
-    *k_out = k;
+    const int st = status_from_kernel(*(uint32_t *)(ctx->h_res + (size_t)R_COUNT * np));
+    if (st != ED_OK) {
+        unsigned long long dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        cudaMemcpy(dg, (char *)ctx->ctl.p + offsetof(LaunchCtl, diag), sizeof(dg), cudaMemcpyDeviceToHost);
+        char buf[256];
+        std::snprintf(buf, sizeof(buf), "kernel wait gave up: site %llu cta %llu t %llu want %llx seen %llx %llx %llx",
+                      dg[0], dg[1], dg[2], dg[3], dg[4], dg[5], dg[6]);
+        ctx->last_err = buf;
+        return st;
+    }
+    k.resize(np);
+    for (int i = 0; i < np; i++) {
+        const unsigned long long *R = ctx->h_res + (size_t)R_COUNT * i;
+        k[i] = R[R_K];
+        ctx->last.extensions += count_extensions(jobs[i].n, jobs[i].m, (int64_t)R[R_K]);
+        ctx->last.slide_chars += R[R_SLIDE];
+        ctx->last.compared_bytes += 2ull * (R[R_SLIDE] + R[R_MISMATCH]);
+        ctx->last.long_slides += R[R_LONG];
+        ctx->last.wide_rounds += R[R_WIDE] * (uint64_t)h;
+        ctx->last.hash_queries += R[R_HASHQ];
+        ctx->last.hash_collisions += R[R_HASHCOLL];
+        for (int j = 0; j < 4; j++)
+            ctx->last.phase_ms[j] += (double)R[R_T0 + j] * 1e-6;
+    }
     return ED_OK;
 }
 
-bool bad_len(size_t n) { return n > (size_t)MAX_LEN; }
+// One pair, device strings, on stream s (the whole grid as one group).
+int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
+             cudaStream_t s, int32_t *dump, int64_t dump_tmax, uint64_t *k_out)
+{
+    int r;
+    TileJob j{dA, dB, n, m, nullptr, nullptr, dump, dump_tmax};
+    if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
+        CK(cudaEventRecord(ctx->ev2, s));
+        if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
+            return r;
+        j.TA = (const uint64_t *)ctx->hashA.p;
+        j.TB = (const uint64_t *)ctx->hashB.p;
+    }
+    std::vector<uint64_t> k;
+    if ((r = run_tiles(ctx, {j}, ctx->grid, s, k)) != ED_OK)
+        return r;
+    if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
+        float bms = 0.f;
+        cudaEventElapsedTime(&bms, ctx->ev2, ctx->ev0);
+        ctx->last.build_ms += bms;
+    }
+    ctx->last.k = k[0];
+    *k_out = k[0];
+    return ED_OK;
+}
 
 } // namespace
 
@@ -379,14 +426,9 @@ int ed_config_default(ed_config *cfg)
         return ED_EINVAL;
     std::memset(cfg, 0, sizeof(*cfg));
     cfg->device = -1;
-    cfg->mem_budget_bytes = 0;
     cfg->max_inflight = 1024;
     cfg->lcp_mode = ED_LCP_AUTO;
-    cfg->hash_seed = 0;
     cfg->spin_limit_ns = 2000000000ull;
-    cfg->grid_ctas = 0;
-    cfg->narrow_width = 0;
-    cfg->max_rounds = 0;
     return ED_OK;
 }
 
@@ -407,7 +449,8 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
         c->cfg.spin_limit_ns = 2000000000ull;
     if (c->cfg.max_inflight <= 0)
         c->cfg.max_inflight = 1024;
-    if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 2)
+    if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 2 || c->cfg.tile_width < 0 || c->cfg.block_rounds < 0 ||
+        c->cfg.tile_width > SMAX_LIMIT)
         return ED_EINVAL;
     int dev = c->cfg.device;
     if (dev < 0)
@@ -418,21 +461,19 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     c->budget = c->cfg.mem_budget_bytes ? c->cfg.mem_budget_bytes : (size_t)(fr * 0.6);
-    // co-resident grid for the cooperative single-pair kernel: one
-    // 1024-thread CTA per SM
-    c->coop_grid = c->cfg.grid_ctas > 0 ? std::min(c->cfg.grid_ctas, c->num_sms) : c->num_sms;
-    c->coop_grid = std::min(c->coop_grid, MAX_GRID);
+    // co-resident grid for the cooperative tile kernel: one 512-thread CTA per SM
+    c->grid = c->cfg.grid_ctas > 0 ? std::min(c->cfg.grid_ctas, c->num_sms) : c->num_sms;
+    c->grid = std::min(c->grid, MAX_GRID);
     CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
     CK(cudaEventCreate(&c->ev0));
     CK(cudaEventCreate(&c->ev1));
     CK(cudaEventCreate(&c->ev2));
-    CK(cudaMallocHost((void **)&c->h_res, sizeof(unsigned long long) * 64));
     // hash base: seeded, in [2^8, q-2]
     const uint64_t seed = c->cfg.hash_seed ? c->cfg.hash_seed : 0x5eed2306174610ull;
     c->hash_base = 256 + splitmix(seed) % (Q61H - 2 - 256);
-    c->hash.pow2[0] = c->hash_base;
+    c->pow2[0] = c->hash_base;
     for (int j = 1; j < 62; j++)
-        c->hash.pow2[j] = hmul(c->hash.pow2[j - 1], c->hash.pow2[j - 1]);
+        c->pow2[j] = hmul(c->pow2[j - 1], c->pow2[j - 1]);
     *out = c.release();
     return ED_OK;
 }
@@ -446,18 +487,22 @@ int ed_destroy(ed_ctx *ctx)
     engine_stop(ctx);
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
-    DevBuf *bufs[] = {&ctx->strA, &ctx->strB, &ctx->gf0,   &ctx->gf1,    &ctx->job,    &ctx->items,
-                      &ctx->res,  &ctx->dump, &ctx->hashA, &ctx->hashB,  &ctx->scan,   &ctx->qx,
-                      &ctx->qy,   &ctx->qo,   &ctx->bpairs, &ctx->border, &ctx->bnext, &ctx->bfront,
-                      &ctx->arena_buf, &ctx->s_pairs, &ctx->s_order, &ctx->s_next};
+    DevBuf *bufs[] = {&ctx->strA,  &ctx->strB,   &ctx->gf,    &ctx->ctl,    &ctx->gctl,      &ctx->slots,
+                      &ctx->halo,  &ctx->pdesc,  &ctx->res,   &ctx->dump,   &ctx->hashA,     &ctx->hashB,
+                      &ctx->scan,  &ctx->qx,     &ctx->qy,    &ctx->qo,     &ctx->bpairs,    &ctx->border,
+                      &ctx->bnext, &ctx->bfront, &ctx->arena_buf, &ctx->s_pairs, &ctx->s_order, &ctx->s_next};
     for (DevBuf *b : bufs)
         release(ctx, *b);
     if (ctx->h_res)
         cudaFreeHost(ctx->h_res);
-    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
-    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
-    if (ctx->ev2) cudaEventDestroy(ctx->ev2);
-    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    if (ctx->ev0)
+        cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1)
+        cudaEventDestroy(ctx->ev1);
+    if (ctx->ev2)
+        cudaEventDestroy(ctx->ev2);
+    if (ctx->stream)
+        cudaStreamDestroy(ctx->stream);
     delete ctx;
     return ED_OK;
 }
@@ -472,8 +517,8 @@ int ed_last_stats(ed_ctx *ctx, ed_stats *out)
     return ED_OK;
 }
 
-int ed_distance_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
-                    uint64_t *k, void *stream)
+int ed_distance_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, uint64_t *k,
+                    void *stream)
 {
     if (!ctx || !k || (n && !A) || (m && !B) || bad_len(n) || bad_len(m))
         return ED_EINVAL;
@@ -497,12 +542,12 @@ int ed_distance(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_
         CK(cudaMemcpyAsync(ctx->strA.p, A, n, cudaMemcpyHostToDevice, ctx->stream));
     if (m)
         CK(cudaMemcpyAsync(ctx->strB.p, B, m, cudaMemcpyHostToDevice, ctx->stream));
-    return run_pair(ctx, (const uint8_t *)ctx->strA.p, (int64_t)n, (const uint8_t *)ctx->strB.p,
-                    (int64_t)m, ctx->stream, nullptr, 0, k);
+    return run_pair(ctx, (const uint8_t *)ctx->strA.p, (int64_t)n, (const uint8_t *)ctx->strB.p, (int64_t)m,
+                    ctx->stream, nullptr, 0, k);
 }
 
-int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
-                     int64_t t_max, int32_t *out, uint64_t *k, void *stream)
+int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
+                     int32_t *out, uint64_t *k, void *stream)
 {
     if (!ctx || !k || !out || t_max < 0 || t_max > 4096 || (n && !A) || (m && !B) || bad_len(n) ||
         bad_len(m))
@@ -521,6 +566,11 @@ int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, 
     if (r != ED_OK)
         return r;
     CK(cudaMemcpy(out, ctx->dump.p, cnt * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    // tiles that had not yet seen k may have gone on past round k: the
+    // frontiers after round k are not part of the answer
+    for (int64_t t = (int64_t)kk + 1; t <= t_max; t++)
+        for (int64_t i = 0; i < 2 * t_max + 1; i++)
+            out[t * (2 * t_max + 1) + i] = (int32_t)0xC0C0C0C0;
     *k = kk <= (uint64_t)t_max ? kk : UINT64_MAX;
     return ED_OK;
 }
@@ -536,14 +586,14 @@ int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T, v
     if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
         return r;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, 0, T, ctx->scan.p, sb, s));
+    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, ctx->scan.p, sb, s));
     CK(cudaStreamSynchronize(s));
     return ED_OK;
 }
 
-int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m,
-               const int64_t *x, const int64_t *y, size_t q, int method, const uint64_t *TA,
-               const uint64_t *TB, int64_t *out, void *stream)
+int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, const int64_t *x,
+               const int64_t *y, size_t q, int method, const uint64_t *TA, const uint64_t *TB, int64_t *out,
+               void *stream)
 {
     if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 4 || bad_len(n) || bad_len(m))
         return ED_EINVAL;
@@ -559,20 +609,27 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
     cudaStream_t s = (cudaStream_t)stream;
     int r;
     if (method == 2) {
-        if ((r = ensure(ctx, ctx->items, sizeof(LongItem) * q)) != ED_OK)
+        if ((r = ensure(ctx, ctx->slots, sizeof(JobSlot) * q)) != ED_OK)
             return r;
-        std::vector<LongItem> it(q);
+        std::vector<JobSlot> it(q);
         for (size_t i = 0; i < q; i++) {
-            it[i] = LongItem{};
-            it[i].x = x[i];
-            it[i].y = y[i];
-            it[i].lim = std::min<int64_t>((int64_t)n - x[i], (int64_t)m - y[i]);
-            it[i].result = (unsigned long long)it[i].lim;
+            JobSlot &j = it[i];
+            j = JobSlot{};
+            j.x = x[i];
+            j.y = y[i];
+            j.lim = std::min<int64_t>((int64_t)n - x[i], (int64_t)m - y[i]);
+            j.result = (unsigned long long)j.lim;
+            j.nchunks = (unsigned)((j.lim + CHUNK_BYTES - 1) / CHUNK_BYTES);
+            j.claim = 1ull << 32;
+            j.A = A;
+            j.B = B;
+            j.n = (long long)n;
+            j.m = (long long)m;
         }
-        CK(cudaMemcpyAsync(ctx->items.p, it.data(), sizeof(LongItem) * q, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(ctx->slots.p, it.data(), sizeof(JobSlot) * q, cudaMemcpyHostToDevice, s));
         CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, nullptr, nullptr, (int64_t)q, 2, nullptr,
-                              nullptr, (LongItem *)ctx->items.p, ctx->coop_grid, s));
-        CK(cudaMemcpyAsync(it.data(), ctx->items.p, sizeof(LongItem) * q, cudaMemcpyDeviceToHost, s));
+                              nullptr, (JobSlot *)ctx->slots.p, ctx->grid, s));
+        CK(cudaMemcpyAsync(it.data(), ctx->slots.p, sizeof(JobSlot) * q, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (size_t i = 0; i < q; i++)
             out[i] = (int64_t)it[i].result;
@@ -583,27 +640,73 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
         return r;
     CK(cudaMemcpyAsync(ctx->qx.p, x, 8 * q, cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(ctx->qy.p, y, 8 * q, cudaMemcpyHostToDevice, s));
-    HashArgs H = ctx->hash;
+    HashArgs H{};
     H.TA = TA;
     H.TB = TB;
-    CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, (const int64_t *)ctx->qx.p,
-                          (const int64_t *)ctx->qy.p, (int64_t)q, method, &H, (int64_t *)ctx->qo.p,
-                          nullptr, ctx->coop_grid, s));
+    std::memcpy(H.pow2, ctx->pow2, sizeof(H.pow2));
+    CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, (const int64_t *)ctx->qx.p, (const int64_t *)ctx->qy.p,
+                          (int64_t)q, method, &H, (int64_t *)ctx->qo.p, nullptr, ctx->grid, s));
     CK(cudaMemcpyAsync(out, ctx->qo.p, 8 * q, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return ED_OK;
 }
 
 // ------------------------------------------------------------------ batch
+static int batch_launch(ed_ctx *ctx, std::vector<BatchPair> &hp, const std::vector<int32_t> &order,
+                        DevBuf &dpairs, DevBuf &dorder, DevBuf &dnext, cudaStream_t s, uint64_t budget_ns)
+{
+    const size_t np = hp.size();
+    int r;
+    if ((r = ensure(ctx, dpairs, sizeof(BatchPair) * np)) != ED_OK ||
+        (r = ensure(ctx, dorder, sizeof(int32_t) * np)) != ED_OK || (r = ensure(ctx, dnext, 64)) != ED_OK)
+        return r;
+    CK(cudaMemcpyAsync(dpairs.p, hp.data(), sizeof(BatchPair) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(dorder.p, order.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(dnext.p, 0, 64, s));
+    BatchArgs Bg{};
+    Bg.pairs = (BatchPair *)dpairs.p;
+    Bg.order = (const int32_t *)dorder.p;
+    Bg.npairs = (int32_t)np;
+    Bg.W = BATCH_W;
+    Bg.round_budget = 0;
+    Bg.next = (uint32_t *)dnext.p;
+    Bg.t1_cap = 64;
+    Bg.t2_cap = 8192;
+    Bg.spin_ns = ctx->cfg.spin_limit_ns;
+    const size_t smem = lv_batch_smem_bytes(BATCH_W);
+    int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+    occ = std::min(occ, 2048 / lv_batch_threads());
+    CK(cudaEventRecord(ctx->ev0, s));
+    CK(launch_lv_batch(Bg, ctx->num_sms * occ, s, budget_ns));
+    CK(cudaEventRecord(ctx->ev1, s));
+    CK(cudaMemcpyAsync(hp.data(), dpairs.p, sizeof(BatchPair) * np, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->last.kernel_ms += ms;
+    ctx->last.kernel_launches += 1;
+    return ED_OK;
+}
+
+// CTAs per group for pairs parked by the batch kernel: enough that the band
+// of a pair at a few percent edits fits the tiles, and no more groups than
+// pairs.
+static int parked_group_size(ed_ctx *ctx, int64_t nm_max, size_t nparked)
+{
+    int G = 4;
+    while (G < ctx->grid && (int64_t)G * SMAX_LIMIT / 4 < nm_max / 5)
+        G *= 2;
+    while (G < ctx->grid && (size_t)(ctx->grid / G) > nparked)
+        G *= 2;
+    return std::min(G, ctx->grid);
+}
+
 static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const size_t *n,
                       const uint8_t *const *B, const size_t *m, uint64_t *k_out, cudaStream_t s)
 {
     int r;
-    const int W = 4096;
-    const size_t fb = sizeof(int32_t) * (W + 3);
-    if ((r = ensure(ctx, ctx->bpairs, sizeof(BatchPair) * np)) != ED_OK ||
-        (r = ensure(ctx, ctx->border, sizeof(int32_t) * np)) != ED_OK ||
-        (r = ensure(ctx, ctx->bnext, 64)) != ED_OK || (r = ensure(ctx, ctx->bfront, fb * np)) != ED_OK)
+    const size_t fb = sizeof(int32_t) * (BATCH_W + 3);
+    if ((r = ensure(ctx, ctx->bfront, fb * np)) != ED_OK)
         return r;
     std::vector<BatchPair> hp(np);
     std::vector<int32_t> order(np);
@@ -616,43 +719,17 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
         b.m = (int64_t)m[p];
         b.front = (int32_t *)((char *)ctx->bfront.p + fb * p);
         b.t = -1;
-        b.state = 0;
         b.k = -1;
         order[p] = (int32_t)p;
     }
     // longest-processing-time first: longer pairs are claimed first
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return std::max(n[a], m[a]) > std::max(n[b], m[b]);
-    });
-    CK(cudaMemcpyAsync(ctx->bpairs.p, hp.data(), sizeof(BatchPair) * np, cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(ctx->border.p, order.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, s));
-    CK(cudaMemsetAsync(ctx->bnext.p, 0, 64, s));
-    BatchArgs Bg{};
-    Bg.pairs = (BatchPair *)ctx->bpairs.p;
-    Bg.order = (const int32_t *)ctx->border.p;
-    Bg.npairs = (int32_t)np;
-    Bg.W = W;
-    Bg.round_budget = 0;
-    Bg.next = (uint32_t *)ctx->bnext.p;
-    Bg.t1_cap = 64;
-    Bg.t2_cap = 8192;
-    Bg.spin_ns = ctx->cfg.spin_limit_ns;
-    int occ = 0;
-    const size_t smem = lv_batch_smem_bytes(W);
-    // occupancy-sized persistent grid
-    occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
-    occ = std::min(occ, 2048 / lv_batch_threads());
-    const int grid = ctx->num_sms * occ;
-    CK(cudaEventRecord(ctx->ev0, s));
-    CK(launch_lv_batch(Bg, grid, s, 0));
-    CK(cudaEventRecord(ctx->ev1, s));
-    CK(cudaMemcpyAsync(hp.data(), ctx->bpairs.p, sizeof(BatchPair) * np, cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
-    ctx->last.kernel_launches += 1;
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    ctx->last.kernel_ms += ms;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return std::max(n[a], m[a]) > std::max(n[b], m[b]); });
+    if ((r = batch_launch(ctx, hp, order, ctx->bpairs, ctx->border, ctx->bnext, s, 0)) != ED_OK)
+        return r;
     uint64_t ext = 0, slide = 0, mism = 0;
+    std::vector<size_t> parked;
+    int64_t nm_max = 0;
     for (size_t p = 0; p < np; p++) {
         const BatchPair &b = hp[p];
         if (b.state == 1) {
@@ -660,19 +737,27 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
             ext += count_extensions(b.n, b.m, b.k);
             slide += b.slide;
             mism += b.mism;
+        } else {
+            parked.push_back(p);
+            nm_max = std::max<int64_t>(nm_max, std::max(b.n, b.m));
         }
     }
     ed_stats keep = ctx->last;
-    // pairs whose band outgrew one CTA: the single-pair kernel, one by one
-    for (size_t p = 0; p < np; p++) {
-        if (hp[p].state == 1)
-            continue;
-        uint64_t kk = 0;
+    if (!parked.empty()) {
+        // pairs whose band outgrew one CTA: CTA groups of the tile kernel,
+        // largest first, all in one launch
+        std::stable_sort(parked.begin(), parked.end(),
+                         [&](size_t a, size_t b) { return std::max(n[a], m[a]) > std::max(n[b], m[b]); });
+        std::vector<TileJob> jobs;
+        for (size_t p : parked)
+            jobs.push_back(TileJob{A[p], B[p], (int64_t)n[p], (int64_t)m[p], nullptr, nullptr, nullptr, 0});
         ctx->last = ed_stats{};
-        r = run_pair(ctx, A[p], (int64_t)n[p], B[p], (int64_t)m[p], s, nullptr, 0, &kk);
-        if (r != ED_OK)
+        std::vector<uint64_t> kk;
+        const int G = parked_group_size(ctx, nm_max, parked.size());
+        if ((r = run_tiles(ctx, jobs, G, s, kk)) != ED_OK)
             return r;
-        k_out[p] = kk;
+        for (size_t i = 0; i < parked.size(); i++)
+            k_out[parked[i]] = kk[i];
         ext += ctx->last.extensions;
         slide += ctx->last.slide_chars;
         mism += ctx->last.compared_bytes / 2 - ctx->last.slide_chars;
@@ -740,8 +825,9 @@ int ed_distance_batch(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
 }
 
 // ------------------------------------------------------------------ serving
-static constexpr int SERVE_W = 4096;
-
+// One engine step: every live pair gets up to ~2 ms of device time in one
+// launch of the batch kernel (frontiers stay resident in the arena); pairs
+// whose band outgrew one CTA are finished together on tile-kernel groups.
 static void engine_loop(ed_ctx *ctx)
 {
     cudaSetDevice(ctx->device);
@@ -759,6 +845,7 @@ static void engine_loop(ed_ctx *ctx)
                 ctx->pending.pop_front();
             }
         }
+        std::unique_lock<std::mutex> api(ctx->api_mu);
         const size_t L = ctx->live.size();
         hp.resize(L);
         order.resize(L);
@@ -772,86 +859,65 @@ static void engine_loop(ed_ctx *ctx)
             b.m = q->m;
             b.front = (int32_t *)q->front;
             b.t = q->t;
-            b.state = 0;
             b.k = -1;
             order[i] = (int32_t)i;
         }
-        std::unique_lock<std::mutex> api(ctx->api_mu);
-        bool ok = true;
-        ed_ctx *c = ctx;
-        auto chk = [&](cudaError_t e) {
-            if (e != cudaSuccess) {
-                ok = false;
-                c->last_err = cudaGetErrorString(e);
-            }
-        };
-        if (ensure(ctx, ctx->s_pairs, sizeof(BatchPair) * L) != ED_OK ||
-            ensure(ctx, ctx->s_order, sizeof(int32_t) * L) != ED_OK || ensure(ctx, ctx->s_next, 64) != ED_OK)
-            ok = false;
-        if (ok) {
-            chk(cudaMemcpyAsync(ctx->s_pairs.p, hp.data(), sizeof(BatchPair) * L, cudaMemcpyHostToDevice,
-                                ctx->sstream));
-            chk(cudaMemcpyAsync(ctx->s_order.p, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice,
-                                ctx->sstream));
-            chk(cudaMemsetAsync(ctx->s_next.p, 0, 64, ctx->sstream));
-            BatchArgs Bg{};
-            Bg.pairs = (BatchPair *)ctx->s_pairs.p;
-            Bg.order = (const int32_t *)ctx->s_order.p;
-            Bg.npairs = (int32_t)L;
-            Bg.W = SERVE_W;
-            Bg.round_budget = 0;
-            Bg.next = (uint32_t *)ctx->s_next.p;
-            Bg.t1_cap = 64;
-            Bg.t2_cap = 8192;
-            Bg.spin_ns = ctx->cfg.spin_limit_ns;
-            const size_t smem = lv_batch_smem_bytes(SERVE_W);
-            int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
-            occ = std::min(occ, 2048 / lv_batch_threads());
-            // a step gives the live pairs about 2 ms of device time; the
-            // claim order rotates so that every pair is reached
-            const int grid = ctx->num_sms * occ;
-            std::rotate(order.begin(), order.begin() + (ctx->n_steps * (uint64_t)grid) % L, order.end());
-            chk(cudaMemcpyAsync(ctx->s_order.p, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice,
-                                ctx->sstream));
-            chk(launch_lv_batch(Bg, grid, ctx->sstream, 2000000ull));
-            chk(cudaMemcpyAsync(hp.data(), ctx->s_pairs.p, sizeof(BatchPair) * L, cudaMemcpyDeviceToHost,
-                                ctx->sstream));
-            chk(cudaStreamSynchronize(ctx->sstream));
-        }
+        const size_t smem = lv_batch_smem_bytes(BATCH_W);
+        int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
+        occ = std::min(occ, 2048 / lv_batch_threads());
+        const uint64_t grid = (uint64_t)ctx->num_sms * occ;
+        std::rotate(order.begin(), order.begin() + (ctx->n_steps * grid) % L, order.end());
+        const int rc = batch_launch(ctx, hp, order, ctx->s_pairs, ctx->s_order, ctx->s_next, ctx->sstream,
+                                    2000000ull);
         ctx->n_steps++;
+        // pairs parked by the batch kernel: finish them on the tile kernel
+        std::vector<size_t> parked;
+        std::vector<TileJob> jobs;
+        int64_t nm_max = 0;
+        if (rc == ED_OK) {
+            for (size_t i = 0; i < L; i++)
+                if (hp[i].state == 2) {
+                    parked.push_back(i);
+                    jobs.push_back(TileJob{hp[i].A, hp[i].B, hp[i].n, hp[i].m, nullptr, nullptr, nullptr, 0});
+                    nm_max = std::max<int64_t>(nm_max, std::max(hp[i].n, hp[i].m));
+                }
+        }
+        std::vector<uint64_t> kk;
+        int rt = ED_OK;
+        if (!jobs.empty())
+            rt = run_tiles(ctx, jobs, parked_group_size(ctx, nm_max, jobs.size()), ctx->sstream, kk);
+        api.unlock();
         std::vector<Request *> still;
         for (size_t i = 0; i < L; i++) {
             Request *q = ctx->live[i];
             const BatchPair &b = hp[i];
-            int64_t result = ED_ECUDA;
+            int64_t result = 0;
             bool done = false;
-            if (!ok) {
+            if (rc != ED_OK) {
+                result = rc;
                 done = true;
             } else if (b.state == 1) {
                 result = b.k;
                 done = true;
             } else if (b.state == 2) {
-                uint64_t kk = 0;
-                int r = run_pair(ctx, (const uint8_t *)q->dA, q->n, (const uint8_t *)q->dB, q->m,
-                                 ctx->sstream, nullptr, 0, &kk);
-                result = r == ED_OK ? (int64_t)kk : r;
+                const size_t j = (size_t)(std::find(parked.begin(), parked.end(), i) - parked.begin());
+                result = rt == ED_OK ? (int64_t)kk[j] : rt;
                 done = true;
             } else {
                 q->t = b.t;
             }
             if (done) {
-                std::lock_guard<std::mutex> lk(ctx->smu);
-                ctx->results[q->ticket] = result;
-                ctx->n_completed++;
                 ctx->arena.release(q->dA, q->bytesA);
                 ctx->arena.release(q->dB, q->bytesB);
                 ctx->arena.release(q->front, q->bytesF);
+                std::lock_guard<std::mutex> lk(ctx->smu);
+                ctx->results[q->ticket] = result;
+                ctx->n_completed++;
                 delete q;
             } else {
                 still.push_back(q);
             }
         }
-        api.unlock();
         std::lock_guard<std::mutex> lk(ctx->smu);
         ctx->live.swap(still);
     }
@@ -859,9 +925,9 @@ static void engine_loop(ed_ctx *ctx)
 
 static int engine_start(ed_ctx *ctx)
 {
+    std::lock_guard<std::mutex> g(ctx->api_mu);
     if (ctx->engine_on)
         return ED_OK;
-    std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -920,7 +986,7 @@ int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t 
     q->m = (int64_t)m;
     q->bytesA = n + 64;
     q->bytesB = m + 64;
-    q->bytesF = sizeof(int32_t) * (SERVE_W + 3);
+    q->bytesF = sizeof(int32_t) * (BATCH_W + 3);
     q->dA = ctx->arena.alloc(q->bytesA);
     q->dB = q->dA ? ctx->arena.alloc(q->bytesB) : nullptr;
     q->front = q->dB ? ctx->arena.alloc(q->bytesF) : nullptr;
@@ -963,11 +1029,8 @@ int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k)
         return ED_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->smu);
     auto it = ctx->results.find(ticket);
-    if (it == ctx->results.end()) {
-        if (ctx->known.count(ticket))
-            return ED_EAGAIN;
-        return ED_ENOTFOUND;
-    }
+    if (it == ctx->results.end())
+        return ctx->known.count(ticket) ? ED_EAGAIN : ED_ENOTFOUND;
     const int64_t v = it->second;
     ctx->results.erase(it);
     ctx->known.erase(ticket);
@@ -983,10 +1046,14 @@ int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed, uint
     if (!ctx)
         return ED_EINVAL;
     std::lock_guard<std::mutex> lk(ctx->smu);
-    if (admitted) *admitted = ctx->n_admitted;
-    if (completed) *completed = ctx->n_completed;
-    if (inflight) *inflight = ctx->live.size() + ctx->pending.size();
-    if (steps) *steps = ctx->n_steps;
+    if (admitted)
+        *admitted = ctx->n_admitted;
+    if (completed)
+        *completed = ctx->n_completed;
+    if (inflight)
+        *inflight = ctx->live.size() + ctx->pending.size();
+    if (steps)
+        *steps = ctx->n_steps;
     return ED_OK;
 }
 

@@ -50,7 +50,7 @@ __device__ __forceinline__ HPair hcat(HPair a, HPair b)
 }
 
 __global__ void __launch_bounds__(HT) prefix_hash_kernel(const uint8_t *X, int64_t len, uint64_t base,
-                                                         uint64_t base_pow_tile, uint64_t *T,
+                                                         uint64_t *T,
                                                          ScanState *st, uint64_t spin_ns)
 {
     __shared__ HPair s_pair[HT];
@@ -159,17 +159,17 @@ __global__ void __launch_bounds__(HT) prefix_hash_kernel(const uint8_t *X, int64
         h = addmod61(mulmod61(h, base), (uint64_t)c[i] + 1);
         T[s0 + i + 1] = h;
     }
-    (void)base_pow_tile;
+
 }
 
-cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t base_pow_tile,
+cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base,
                                uint64_t *T, void *scan_state, size_t scan_state_bytes, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(scan_state, 0, scan_state_bytes, s);
     if (e != cudaSuccess)
         return e;
     const int64_t tiles = len == 0 ? 1 : (len + TILE_CHARS - 1) / TILE_CHARS;
-    prefix_hash_kernel<<<(unsigned)tiles, HT, 0, s>>>(X, len, base, base_pow_tile, T,
+    prefix_hash_kernel<<<(unsigned)tiles, HT, 0, s>>>(X, len, base, T,
                                                       reinterpret_cast<ScanState *>(scan_state),
                                                       2000000000ull);
     return cudaGetLastError();

@@ -10,75 +10,103 @@ namespace edg {
 constexpr uint32_t ST_TIMEOUT = 4;
 constexpr uint32_t ST_LIMIT = 7;
 
-constexpr int MAX_GRID = 1024;   // helper slots in the job block
-constexpr int CTA_THREADS = 512;
-constexpr int CHUNK_BYTES = CTA_THREADS * 16 * 4; // whole-grid slide chunk
+constexpr int CTA_THREADS = 512;   // threads of a tile CTA
+constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
+constexpr int HMAX = 16;           // rounds per temporal block, at most
+constexpr int CHUNK_UNROLL = 8;
+constexpr int CHUNK_BYTES = CTA_THREADS * 16 * CHUNK_UNROLL; // 64 KiB per claim
+constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
+constexpr uint32_t CLAIM_CLOSED = 0xffffffffu;
 
-// A slide that outgrew one warp, handed to the whole grid.  result starts
-// at lim and is lowered with atomicMin to the first mismatch offset.
-struct LongItem {
-    int64_t x, y, lim;
+// A long slide open for help.  Each CTA owns one slot.  `claim` packs the
+// job id (high 32 bits) and the next unclaimed 64 KiB chunk (low 32 bits,
+// CLAIM_CLOSED once the owner closed it); chunks are claimed by CAS in
+// increasing order; `result` (first mismatch offset, starts at lim) falls
+// by atomicMin; `done` counts finished claims.
+struct __align__(128) JobSlot {
+    unsigned long long claim;
     unsigned long long result;
-    int32_t d;
+    long long x, y, lim;
+    unsigned int done, nchunks;
+    const uint8_t *A, *B; // the strings compared (any pair of the launch)
+    long long n, m;
+};
+
+// One pair of a tile launch.
+struct PairDesc {
+    const uint8_t *A, *B;
+    int64_t n, m;
+    const uint64_t *TA, *TB;   // prefix-hash tables (hash LCP) or null
+    unsigned long long *res;   // R_COUNT counters of this pair
+    int32_t *dump;             // frontier dump (tests) or null
+    int32_t dump_tmax;
     int32_t pad;
 };
 
-// Control block of one single-pair launch (zeroed before the launch).
-struct LvJob {
-    uint32_t epoch;     // last job published by CTA 0 (release)
-    uint32_t kind;      // JOB_*
-    uint32_t nitems;    // items of a JOB_LONG
-    uint32_t wide_t;    // first round of the wide phase
-    uint32_t error;     // kernel status (0 = ok)
-    uint32_t bar_count; // grid barrier arrivals
-    uint32_t bar_gen;   // grid barrier generation
-    uint32_t glist[3];  // wide-phase long-item counts, by round mod 3
-    uint32_t pad[6];
-    uint32_t done[MAX_GRID]; // helper h: last epoch it finished
+// Per group of CTAs (zeroed before the launch).
+struct __align__(64) GroupCtl {
+    unsigned long long done_k; // ~0 until the tile owning d = m - n finds k
+    uint32_t bar_count, bar_gen;
+    uint32_t epoch_req;        // epoch changes requested (for CTAs without a tile)
+    uint32_t epoch_t;          // round at which the last epoch change happens
+    int32_t pair;              // pair index being run (-1: none left)
+    uint32_t ebar_count, ebar_gen; // epoch-change barrier (abandoned once k is known)
+    uint32_t pad[7];
 };
-enum : uint32_t { JOB_NONE = 0, JOB_LONG = 1, JOB_WIDE = 2, JOB_QUIT = 3 };
 
-// Result counters written by a launch.
+// Per launch (zeroed before the launch).
+struct __align__(64) LaunchCtl {
+    uint32_t error;
+    uint32_t queue;            // next pair of the queue
+    uint32_t pad[14];
+    // where the first failed wait gave up: site, CTA, round, awaited value,
+    // values seen, done_k
+    unsigned long long diag[8];
+    unsigned long long active[(MAX_GRID + 63) / 64]; // job slots open for help
+    // per CTA: (pair iteration << 32) | first round not yet published
+    unsigned long long flags[MAX_GRID];
+};
+
+// Result counters written by a launch, per pair.
 enum {
     R_K = 0,
     R_SLIDE = 1,      // sum of LCP lengths
     R_MISMATCH = 2,   // slides that ended on a mismatching pair
-    R_LONG = 3,       // long slides given to the grid
-    R_WIDE = 4,       // rounds run in the wide phase
+    R_LONG = 3,       // slides given to the job slots
+    R_WIDE = 4,       // temporal blocks run
     R_HASHQ = 5,
     R_HASHCOLL = 6,
     R_STATUS = 7,
-    R_COUNT = 8
+    // device time (ns, seen by thread 0 of the group's first CTA): rounds,
+    // open slides, halo waits (helping included), epoch changes, spare
+    R_T0 = 8,
+    R_COUNT = 14
 };
 
-struct HashArgs {
-    const uint64_t *TA, *TB; // prefix tables (n+1, m+1 entries) or null
-    uint64_t pow2[62];       // p^(2^j) mod 2^61-1
-};
-
-struct PairArgs {
-    const uint8_t *A, *B;
-    int64_t n, m;
-    int32_t kcap;       // rounds the wide frontier can hold
-    int32_t W0;         // narrow band capacity (even); t <= W0/2 in narrow mode
-    int32_t *gf0, *gf1; // wide frontiers, 2*kcap+5 entries each (no clearing
-                        // needed: every round writes its band and sentinels)
-    LvJob *job;
-    LongItem *items;
-    int32_t item_cap;
-    int32_t t1_cap;     // bytes one thread examines before escalating
-    int32_t t2_cap;     // bytes one warp examines before escalating
+struct LvArgs {
+    const PairDesc *pairs;
+    int32_t npairs;
+    int32_t group_size;   // CTAs per group; groups = gridDim.x / group_size
+    GroupCtl *gctl;
+    LaunchCtl *ctl;
+    JobSlot *slots;       // gridDim.x slots
+    int32_t *halo;        // [gridDim.x][2 parity][2 sides][HMAX]
+    int32_t *gf;          // per group: 2 buffers of 2*kcap+5 entries
+    int64_t gf_stride;    // entries per group (2 buffers)
+    int32_t kcap;         // largest epoch radius the buffers hold
+    int32_t smax;         // tile width capacity (shared memory)
+    int32_t h;            // rounds per temporal block (1..HMAX)
+    int32_t s0;           // initial tile width
+    int32_t t1_cap;       // bytes one thread examines before escalating
+    int32_t t2_cap;       // bytes one warp examines before escalating
     int32_t use_hash;
-    HashArgs hash;
-    unsigned long long *res; // R_COUNT counters
-    int32_t *dump;           // frontier dump or null
-    int32_t dump_tmax;
-    uint64_t spin_ns;  // bound of one wait for a peer
-    uint64_t idle_ns;  // bound of a helper's wait for the next job
+    uint64_t pow2[62];    // p^(2^j) mod 2^61-1 (hash LCP)
+    uint64_t spin_ns;     // bound of one wait on a peer's progress
+    uint64_t idle_ns;     // bound of a wait that may span other CTAs' work
 };
 
-size_t lv_single_smem_bytes(int W0);
-cudaError_t launch_lv_single(const PairArgs &P, int grid, cudaStream_t s);
+size_t lv_tiles_smem_bytes(int smax, int h);
+cudaError_t launch_lv_tiles(const LvArgs &P, int grid, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch
 // One pair of a batch / serving slot.  Frontier state lives in global
@@ -88,7 +116,7 @@ struct BatchPair {
     int64_t n, m;
     int32_t *front;    // W + 3 int32: the pair's resident frontier (round t)
     int32_t t;         // rounds completed so far (-1 = not started)
-    int32_t state;     // 0 running, 1 done, 2 needs the single-pair kernel
+    int32_t state;     // 0 running, 1 done, 2 needs the tile kernel
     int64_t k;
     unsigned long long slide, mism;
 };
@@ -112,17 +140,22 @@ cudaError_t launch_lv_batch(const BatchArgs &B, int grid, cudaStream_t s, uint64
 int lv_batch_threads();
 
 // ---------------------------------------------------------------- tests
-// method 2 reads queries from items[0..q) (x, y, lim, result = lim) and
-// leaves the answers in items[i].result; the others use x, y, out.
+struct HashArgs {
+    const uint64_t *TA, *TB;
+    uint64_t pow2[62];
+};
+// LCP queries by the building blocks: 0 per thread, 1 per warp, 2 whole
+// grid (job slots), 3 hash search alone, 4 hash + direct confirmation.
+// Method 2 reads queries from slots[0..q) (x, y, lim) and leaves answers in
+// slots[i].result; the others use x, y, out.
 cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
                                const int64_t *x, const int64_t *y, int64_t q, int method,
-                               const HashArgs *hash, int64_t *out, LongItem *items, int grid,
+                               const HashArgs *hash, int64_t *out, JobSlot *slots, int grid,
                                cudaStream_t s);
 
 // ---------------------------------------------------------------- hash
-cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t base_pow_tile,
-                               uint64_t *T, void *scan_state, size_t scan_state_bytes,
-                               cudaStream_t s);
+cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T,
+                               void *scan_state, size_t scan_state_bytes, cudaStream_t s);
 size_t prefix_hash_state_bytes(int64_t len);
 
 } // namespace edg

@@ -11,15 +11,17 @@ from paper_2306_17461_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# kernel configurations exercised: default; a tiny narrow band so the whole
-# grid takes over after a few rounds; few CTAs; the hash LCP
+# kernel configurations exercised: default; narrow first tiles (many epoch
+# changes, the band crosses many tiles); one round per block; odd block
+# lengths and few CTAs; one CTA; the hash LCP
 CONFIGS = {
     "default": {},
-    "wide": {"narrow_width": 8},
-    "wide_g3": {"narrow_width": 4, "grid_ctas": 3},
+    "wide": {"tile_width": 1, "block_rounds": 4},
+    "wide_g3": {"tile_width": 2, "grid_ctas": 3, "block_rounds": 3},
+    "h1": {"block_rounds": 1, "tile_width": 1},
     "one_cta": {"grid_ctas": 1},
     "hash": {"lcp_mode": 2},
-    "hash_wide": {"lcp_mode": 2, "narrow_width": 6},
+    "hash_wide": {"lcp_mode": 2, "tile_width": 1, "block_rounds": 5},
 }
 
 
