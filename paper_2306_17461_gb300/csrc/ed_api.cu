@@ -128,6 +128,7 @@ struct ed_ctx {
     int device = 0;
     int num_sms = 0;
     int grid = 0; // CTAs of the tile kernel
+    int clock_khz = 1;
     cudaStream_t stream = nullptr;
     std::string last_err;
     size_t budget = 0;
@@ -324,7 +325,7 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
     P.h = h;
     P.s0 = s0;
     P.t1_cap = 64;
-    P.t2_cap = 2048;
+    P.t2_cap = 4096;
     P.use_hash = jobs[0].TA != nullptr;
     std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
     P.spin_ns = ctx->cfg.spin_limit_ns;
@@ -351,7 +352,7 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
         unsigned long long dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         cudaMemcpy(dg, (char *)ctx->ctl.p + offsetof(LaunchCtl, diag), sizeof(dg), cudaMemcpyDeviceToHost);
         char buf[256];
-        std::snprintf(buf, sizeof(buf), "kernel wait gave up: site %llu cta %llu t %llu want %llx seen %llx %llx %llx",
+        std::snprintf(buf, sizeof(buf), "kernel check failed: site %llu cta %llu t %llu want %llx seen %llx %llx %llx",
                       dg[0], dg[1], dg[2], dg[3], dg[4], dg[5], dg[6]);
         ctx->last_err = buf;
         return st;
@@ -367,8 +368,12 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
         ctx->last.wide_rounds += R[R_WIDE] * (uint64_t)h;
         ctx->last.hash_queries += R[R_HASHQ];
         ctx->last.hash_collisions += R[R_HASHCOLL];
+        // SM cycles -> ms at the device's nominal clock
+        const double per_ms = (double)ctx->clock_khz;
         for (int j = 0; j < 4; j++)
-            ctx->last.phase_ms[j] += (double)R[R_T0 + j] * 1e-6;
+            ctx->last.phase_ms[j] += (double)R[R_T0 + j] / per_ms;
+        if (R[R_T0 + 5])
+            ctx->last.phase_ms[4] += (double)R[R_T0 + 4] / (double)R[R_T0 + 5] / per_ms;
     }
     return ED_OK;
 }
@@ -458,6 +463,8 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
     CK(cudaSetDevice(dev));
     c->device = dev;
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CK(cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, dev));
+    c->clock_khz = std::max(c->clock_khz, 1);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
     c->budget = c->cfg.mem_budget_bytes ? c->cfg.mem_budget_bytes : (size_t)(fr * 0.6);
@@ -685,6 +692,14 @@ static int batch_launch(ed_ctx *ctx, std::vector<BatchPair> &hp, const std::vect
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->last.kernel_ms += ms;
     ctx->last.kernel_launches += 1;
+    for (size_t i = 0; i < np; i++)
+        if (hp[i].state == 3) {
+            char buf[200];
+            std::snprintf(buf, sizeof(buf), "batch self-check: pair %zu round %lld diagonal %lld start row %lld", i,
+                          (long long)hp[i].check[0], (long long)hp[i].check[1], (long long)hp[i].check[2]);
+            ctx->last_err = buf;
+            return ED_ECUDA;
+        }
     return ED_OK;
 }
 

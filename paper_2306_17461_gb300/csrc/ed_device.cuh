@@ -154,6 +154,51 @@ __device__ __forceinline__ int64_t slide_thread_w(const uint8_t *A, int64_t n, c
     return l;
 }
 
+// The word part of slide_thread_w alone: returns the matched length when
+// the words decide the slide (a mismatch within them, or lim reached), else
+// -1 with *avail = the bytes they showed equal.
+__device__ __forceinline__ int64_t word_slide(const uint8_t *A, const uint8_t *B, int64_t x, int64_t y,
+                                              int64_t lim, uint32_t wa, uint32_t wb, int64_t *avail)
+{
+    if (lim <= 0)
+        return 0;
+    const uint32_t sa = (uint32_t)((uintptr_t)(A + x) & 3), sb = (uint32_t)((uintptr_t)(B + y) & 3);
+    wa >>= 8 * sa;
+    wb >>= 8 * sb;
+    int64_t av = (int64_t)(4 - max(sa, sb));
+    if (av > lim)
+        av = lim;
+    const uint32_t mask = av >= 4 ? 0xffffffffu : ((1u << (8 * av)) - 1u);
+    const uint32_t dif = (wa ^ wb) & mask;
+    if (dif)
+        return (__ffs((int)dif) - 1) >> 3;
+    if (av >= lim)
+        return lim;
+    *avail = av;
+    return -1;
+}
+
+// The 16-byte window part of slide_thread_w, from l bytes already equal.
+static __device__ __noinline__ int64_t slide_more(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
+                                           int64_t x, int64_t y, int64_t l, int64_t lim, int64_t cap,
+                                           bool *open)
+{
+    *open = false;
+    const int64_t stop = min(lim, cap);
+    while (l < stop) {
+        const uint4 va = load16(A, n, x + l);
+        const uint4 vb = load16(B, m, y + l);
+        const int f = first_diff16(va, vb);
+        if (f < 16)
+            return min(l + f, lim);
+        l += 16;
+    }
+    if (l >= lim)
+        return lim;
+    *open = true;
+    return l;
+}
+
 __device__ __forceinline__ int64_t slide_thread(const uint8_t *A, int64_t n, const uint8_t *B,
                                                 int64_t m, int64_t x, int64_t y, int64_t lim,
                                                 int64_t cap, bool *open)

@@ -120,8 +120,15 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
                 outcome = 2;
                 break;
             }
-            if (rounds_here > 0 && ((Bg.round_budget > 0 && rounds_here >= Bg.round_budget) ||
-                                    (deadline_ns != 0 && gtimer() >= deadline_ns))) {
+            // the budget decision is taken by one thread for the whole CTA:
+            // threads reading the timer apart must not leave the loop apart
+            if (tid == 0)
+                *S.flag = rounds_here > 0 && ((Bg.round_budget > 0 && rounds_here >= Bg.round_budget) ||
+                                              (deadline_ns != 0 && gtimer() >= deadline_ns));
+            __syncthreads();
+            const int spent = *S.flag;
+            __syncthreads();
+            if (spent) {
                 outcome = 0;
                 break;
             }
@@ -138,6 +145,15 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
                     const int64_t e = (int64_t)prev[d + H + 1 + 1] + 1;
                     c = max(a, max(b, e));
                     c = min(c, min(n, m - d));
+                }
+                if (c < 0 || c + d < 0) {
+                    // a start row outside the grid: record it, never load it
+                    Pr.check[0] = t;
+                    Pr.check[1] = d;
+                    Pr.check[2] = c;
+                    Pr.state = 3;
+                    cur[d + H + 1] = NEG;
+                    continue;
                 }
                 const int64_t full = min(n - c, m - c - d);
                 bool open;
@@ -201,7 +217,8 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
                 if (tid == 0)
                     *S.n1 = 0;
             }
-            const bool fin = (target >= lo && target <= hi) && cur[target + H + 1] == n;
+            const bool fin = ((target >= lo && target <= hi) && cur[target + H + 1] == n) ||
+                             *(volatile int32_t *)&Pr.state == 3;
             __syncthreads();
             if (fin) {
                 outcome = 1;
@@ -217,7 +234,12 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
             if (slide) atomicAdd(&Pr.slide, slide);
             if (mism) atomicAdd(&Pr.mism, mism);
         }
-        if (outcome == 1) {
+        __syncthreads();
+        const bool failed = *(volatile int32_t *)&Pr.state == 3;
+        __syncthreads();
+        if (failed) {
+            // leave the self-check record for the host
+        } else if (outcome == 1) {
             if (tid == 0) {
                 Pr.k = t;
                 Pr.t = (int32_t)t;

@@ -116,9 +116,10 @@ struct BatchPair {
     int64_t n, m;
     int32_t *front;    // W + 3 int32: the pair's resident frontier (round t)
     int32_t t;         // rounds completed so far (-1 = not started)
-    int32_t state;     // 0 running, 1 done, 2 needs the tile kernel
+    int32_t state;     // 0 running, 1 done, 2 needs the tile kernel, 3 self-check failed
     int64_t k;
     unsigned long long slide, mism;
+    long long check[3]; // self-check record: round, diagonal, start row
 };
 
 struct BatchArgs {

@@ -21,18 +21,23 @@
 //    There is no grid-wide barrier per round, only neighbour waits every h
 //    rounds.
 //  * Slides: one thread compares the leading 4-byte words (several
-//    diagonals' loads in flight together), then 16-byte windows; a slide
-//    still open after t1_cap bytes goes to one warp (ballot / first set
-//    bit over 512-byte steps); one still open after t2_cap bytes becomes a
-//    job in the CTA's job slot, split into 64 KiB chunks that the owner and
-//    every CTA waiting on a neighbour (or without a tile) claim by CAS;
-//    the first mismatch is the atomicMin over chunks.
-//  * Every wait is bounded by %globaltimer and reports ST_TIMEOUT instead
-//    of hanging.
+//    diagonals' loads in flight together), then 16-byte windows; slides
+//    still open after t1_cap bytes go to one warp each (ballot / first set
+//    bit over 512-byte steps) or, when few, straight to the whole CTA, which
+//    scans 64 KiB per step with every load in flight.  A slide still open
+//    after LOCAL_STEPS such steps becomes a job in the CTA's job slot: its
+//    64 KiB chunks are claimed by atomicAdd by the owner and by every CTA
+//    that is waiting on a neighbour or has no tile; the first mismatch is the
+//    atomicMin over chunks.
+//  * Every wait is bounded by %globaltimer and reports ST_TIMEOUT (with the
+//    place it gave up) instead of hanging.
 #include "ed_device.cuh"
 #include "lv_kernels.cuh"
 
 namespace edg {
+
+constexpr int LOCAL_STEPS = 4;            // 64 KiB steps the owner takes alone
+constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
 struct Counters {
     unsigned long long slide = 0, mism = 0, hashq = 0, coll = 0, longs = 0, blocks = 0;
@@ -108,60 +113,6 @@ struct Pair {
     bool hash;
 };
 
-// ------------------------------------------------------------------ phase A
-constexpr int DPT = 4; // diagonals per thread per batch
-
-// One round over diagonals [lo, hi] (strided over the CTA): the start row
-// c = getc(d), then the per-thread slide.  DPT diagonals per thread are
-// handled together so that their first loads are in flight together.
-// done(d, c, l, full) receives finished slides (row c + l); open_(d, c, pos,
-// lim_abs) receives slides still open after t1_cap bytes (A[c..pos) matched,
-// the first mismatch lies in [pos, lim_abs], lim_abs possibly lowered to
-// the hash answer + 1).
-template <class GetC, class Done, class Open>
-__device__ __forceinline__ void phase_a(const LvArgs &P, const Pair &Q, int64_t lo, int64_t hi,
-                                        GetC getc, Done done, Open open_, Counters &C)
-{
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t base = lo; base <= hi; base += (int64_t)nt * DPT) {
-        int64_t c[DPT];
-        uint32_t wa[DPT], wb[DPT];
-#pragma unroll
-        for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            c[u] = 0;
-            wa[u] = wb[u] = 0;
-            if (d <= hi) {
-                c[u] = getc(d);
-                if (min(Q.n - c[u], Q.m - c[u] - d) > 0)
-                    word_load(Q.A, Q.B, c[u], c[u] + d, wa[u], wb[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            if (d <= hi) {
-                const int64_t cc = c[u];
-                const int64_t full = min(Q.n - cc, Q.m - cc - d);
-                bool op;
-                const int64_t l = slide_thread_w(Q.A, Q.n, Q.B, Q.m, cc, cc + d, full, P.t1_cap,
-                                                 wa[u], wb[u], &op);
-                if (!op) {
-                    done(d, cc, l, full);
-                } else {
-                    int64_t lim = full;
-                    if (Q.hash) {
-                        const int64_t h = hash_lcp(P.pow2, Q.TA, Q.TB, cc, cc + d, l, full);
-                        C.hashq++;
-                        lim = min(h + 1, full);
-                    }
-                    open_(d, cc, cc + l, cc + lim);
-                }
-            }
-        }
-    }
-}
-
 // An open slide of diagonal d (start row c) reached row p: a mismatch at
 // p < lim_abs, or none before lim_abs (p == lim_abs).  Returns the final
 // row.  When the hash bound cut the search short and the direct compare
@@ -184,6 +135,102 @@ __device__ __forceinline__ int64_t finish_slide(const Pair &Q, int64_t c, int64_
         C.mism += (p < full_abs);
     }
     return p;
+}
+
+// ------------------------------------------------------------------ phase A
+constexpr int DPT = 4; // diagonals per thread per batch
+
+struct RoundArgs {
+    const uint8_t *A, *B;
+    int64_t n, m;
+    const int32_t *prev;     // round tau-1, indexed d - off
+    int32_t *cur;            // round tau
+    int64_t off, lo, hi, tau, a, b;
+    int t1_cap;
+    int *n1;
+    int32_t *open;           // diagonals whose slide is still open
+    uint32_t *err;           // launch status word (self-check records)
+    unsigned long long *diag;
+};
+struct RoundCount {
+    unsigned long long slide, mism;
+};
+
+// The start row of diagonal d in round tau from the three predecessors,
+// clamped to the diagonal's last cell.
+__device__ __forceinline__ int64_t start_row(const int32_t *prev, int64_t off, int64_t d, int64_t tau,
+                                             int64_t n, int64_t m)
+{
+    if (tau == 0)
+        return 0;
+    const int64_t x1 = prev[d - 1 - off];
+    const int64_t x2 = (int64_t)prev[d - off] + 1;
+    const int64_t x3 = (int64_t)prev[d + 1 - off] + 1;
+    return min(max(x1, max(x2, x3)), min(n, m - d));
+}
+
+// One round over diagonals [lo, hi] of the tile (strided over the CTA): the
+// start row, then the per-thread slide.  DPT diagonals per thread are
+// handled together so that their first loads are in flight together.
+// Diagonals whose slide is still open after t1_cap bytes are listed; the
+// list holds one entry per computed diagonal at most, so it cannot fill.
+// Counts only diagonals of [a, b).
+__device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
+{
+    RoundCount out = {0, 0};
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int64_t base = R.lo; base <= R.hi; base += (int64_t)nt * DPT) {
+        int64_t c[DPT];
+        uint32_t wa[DPT], wb[DPT];
+#pragma unroll
+        for (int u = 0; u < DPT; u++) {
+            const int64_t d = base + (int64_t)u * nt + tid;
+            c[u] = 0;
+            wa[u] = wb[u] = 0;
+            if (d <= R.hi) {
+                c[u] = start_row(R.prev, R.off, d, R.tau, R.n, R.m);
+                if (c[u] < 0 || c[u] + d < 0) {
+                    // a start row outside the grid: record it, never load it
+                    if (atomicCAS(R.err, 0u, 6u) == 0u) {
+                        R.diag[0] = 6;
+                        R.diag[1] = blockIdx.x;
+                        R.diag[2] = (unsigned long long)R.tau;
+                        R.diag[3] = (unsigned long long)d;
+                        R.diag[4] = (unsigned long long)c[u];
+                        R.diag[5] = ((unsigned long long)(uint32_t)R.prev[d - 1 - R.off] << 32) |
+                                    (uint32_t)R.prev[d + 1 - R.off];
+                        R.diag[6] = (unsigned long long)R.off;
+                    }
+                    c[u] = 0;
+                } else if (min(R.n - c[u], R.m - c[u] - d) > 0) {
+                    word_load(R.A, R.B, c[u], c[u] + d, wa[u], wb[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < DPT; u++) {
+            const int64_t d = base + (int64_t)u * nt + tid;
+            if (d <= R.hi) {
+                const int64_t cc = c[u];
+                const int64_t full = min(R.n - cc, R.m - cc - d);
+                bool op = false;
+                int64_t av = 0;
+                int64_t l = word_slide(R.A, R.B, cc, cc + d, full, wa[u], wb[u], &av);
+                if (l < 0) // rare: the words matched; 16-byte windows, out of line
+                    l = slide_more(R.A, R.n, R.B, R.m, cc, cc + d, av, full, R.t1_cap, &op);
+                if (!op) {
+                    R.cur[d - R.off] = (int32_t)(cc + l);
+                    if (d >= R.a && d < R.b) {
+                        out.slide += l;
+                        out.mism += (l < full);
+                    }
+                } else {
+                    R.open[atomicAdd(R.n1, 1)] = (int32_t)d;
+                }
+            }
+        }
+    }
+    return out;
 }
 
 // ------------------------------------------------------------------ jobs
@@ -220,38 +267,40 @@ __device__ __noinline__ void wait_failed(const LvArgs &P, unsigned long long sit
     }
 }
 
-// Claim the next chunk of slot sl (thread 0).  Returns the chunk index, -1
-// when there is nothing left to claim (closed, past the end, or past the
-// first mismatch found so far), -2 when the CAS lost a race.
-__device__ int64_t try_claim(JobSlot *sl)
-{
-    const unsigned long long w = ld_acquire_u64(&sl->claim);
-    const uint32_t c = (uint32_t)w;
-    if (c == CLAIM_CLOSED || (w >> 32) == 0)
-        return -1;
-    const uint32_t nch = *(volatile unsigned int *)&sl->nchunks;
-    const unsigned long long res = *(volatile unsigned long long *)&sl->result;
-    if (c >= nch || (unsigned long long)c * CHUNK_BYTES >= res)
-        return -1;
-    if (atomicCAS(&sl->claim, w, w + 1) != w)
-        return -2;
-    __threadfence();
-    return (int64_t)c;
-}
-
 struct Smem {
-    int32_t *F[2];      // tile + halo frontier, smax + 2h + 2 entries each
-    int32_t *ld, *lc;   // open slides: diagonal, start row
-    int64_t *lpos, *llim;
+    int32_t *F[2];      // tile + halo frontier, smax + 2*HMAX + 2 entries each
+    int32_t *ld;        // open slides: diagonal (lcap entries)
     int *n1;
     int *bc;            // 8 broadcast words
     long long *bcl;     // 4 broadcast 64-bit words
     unsigned long long *smin;
     int lcap;
+    uint32_t *err;             // launch status word (self-check records)
+    unsigned long long *diag;
 };
 
-// Scan chunk c of slot sl with the whole CTA, lower its result, count it.
-__device__ __noinline__ void scan_chunk(const Smem &S, JobSlot *sl, int64_t c)
+// Job slot protocol.  claim = (job id << 32) | count.  Every atomicAdd of 1
+// is one claim of chunk `count`; a claim whose count has CLAIM_CLOSE set
+// arrived after the owner closed the job and is void.  Each valid claim is
+// answered by exactly one increment of `done` (after scanning the chunk, or
+// at once when the chunk lies past the end or past the best mismatch).  A
+// claim that lands on a job published after the claimer looked is still a
+// valid claim of that job: the descriptor read after the atomic is that
+// job's, because the slot cannot be republished before `done` covers it.
+// Returns the chunk index (>= 0) with the job's descriptor in the slot, or
+// -1 when the claim is void.
+__device__ __forceinline__ int64_t claim_chunk(JobSlot *sl)
+{
+    const unsigned long long w = atomicAdd(&sl->claim, 1ull);
+    __threadfence();
+    if ((w >> 32) == 0 || ((uint32_t)w & CLAIM_CLOSE))
+        return -1;
+    return (int64_t)(uint32_t)w;
+}
+
+// Scan (or skip) claimed chunk c of slot sl with the whole CTA, lower the
+// job's result, answer the claim.
+__device__ __noinline__ void serve_claim(const Smem &S, JobSlot *sl, int64_t c)
 {
     // the slot is rewritten for every job: read it past the L1
     const uint8_t *A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
@@ -259,18 +308,41 @@ __device__ __noinline__ void scan_chunk(const Smem &S, JobSlot *sl, int64_t c)
     const int64_t n = __ldcg(&sl->n), m = __ldcg(&sl->m), x = __ldcg(&sl->x), y = __ldcg(&sl->y),
                   lim = __ldcg(&sl->lim);
     const int64_t cs = c * (int64_t)CHUNK_BYTES;
-    const int64_t r = cta_scan<CHUNK_UNROLL>(A, n, B, m, x, y, cs, min((int64_t)CHUNK_BYTES, lim - cs),
-                                             S.smin);
+    // one thread decides from the job's current best, for the whole CTA
     if (threadIdx.x == 0) {
-        if (r >= 0)
+        *S.bc = (cs < lim && (unsigned long long)cs < *(volatile unsigned long long *)&sl->result) ? 1 : 0;
+        if (x < 0 || y < 0 || lim < 0 || x + lim > n || y + lim > m || !A || !B) {
+            // a job outside its strings: never scan it (self-check record 7)
+            *S.bc = 0;
+            if (S.err && atomicCAS(S.err, 0u, 7u) == 0u) {
+                S.diag[0] = 7;
+                S.diag[1] = blockIdx.x;
+                S.diag[2] = (unsigned long long)x;
+                S.diag[3] = (unsigned long long)y;
+                S.diag[4] = (unsigned long long)lim;
+                S.diag[5] = (unsigned long long)n;
+                S.diag[6] = (unsigned long long)m;
+            }
+        }
+    }
+    __syncthreads();
+    const int go = *S.bc;
+    __syncthreads();
+    if (go) {
+        const int64_t r =
+            cta_scan<4>(A, n, B, m, x, y, cs, min((int64_t)CHUNK_BYTES, lim - cs), S.smin);
+        if (threadIdx.x == 0 && r >= 0)
             atomicMin(&sl->result, (unsigned long long)r);
+    }
+    if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(&sl->done, 1u);
     }
+    __syncthreads();
 }
 
-// Help one open job of any CTA (whole CTA).  Returns true if a chunk was
-// scanned.
+// Help one open job of any CTA (whole CTA).  Returns true if a claim was
+// made.
 __device__ bool help_one(const LvArgs &P, const Smem &S)
 {
     const int tid = threadIdx.x;
@@ -290,9 +362,14 @@ __device__ bool help_one(const LvArgs &P, const Smem &S)
                 const int s = w * 64 + b;
                 if (s >= (int)gridDim.x)
                     continue;
-                int64_t c = try_claim(&P.slots[s]);
-                if (c == -2)
-                    c = try_claim(&P.slots[s]);
+                JobSlot *sl = &P.slots[s];
+                // claim only when the job visibly has chunks left
+                const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
+                const uint32_t cnt = (uint32_t)w0;
+                if ((w0 >> 32) == 0 || (cnt & CLAIM_CLOSE) || cnt >= *(volatile unsigned int *)&sl->nchunks ||
+                    (unsigned long long)cnt * CHUNK_BYTES >= *(volatile unsigned long long *)&sl->result)
+                    continue;
+                const int64_t c = claim_chunk(sl);
                 if (c >= 0) {
                     slot = s;
                     chunk = c;
@@ -308,20 +385,33 @@ __device__ bool help_one(const LvArgs &P, const Smem &S)
     __syncthreads();
     if (slot < 0)
         return false;
-    scan_chunk(S, &P.slots[slot], chunk);
+    serve_claim(S, &P.slots[slot], chunk);
     return true;
 }
 
-// The CTA's own long slide: A[x..x+lim) vs B[y..).  Published in the CTA's
-// slot when it spans more than one chunk; the owner claims chunks like any
-// helper, then closes the slot and waits for the claims still running.
+// The CTA's own long slide: the first mismatch of A[x..x+lim) vs B[y..).
+// The CTA scans LOCAL_STEPS steps of 64 KiB alone; what is left becomes a
+// job in the CTA's slot, claimed chunk by chunk by the CTA and by helpers;
+// the CTA then closes the job and waits for the claims still running.
 // Returns the first mismatch offset, or lim.
 __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const Pair &Q, int64_t x,
-                                           int64_t y, int64_t lim)
+                                           int64_t y, int64_t lim, Counters &C)
 {
     const int tid = threadIdx.x;
+    int64_t off = 0;
+    for (int step = 0; step < LOCAL_STEPS && off < lim; step++) {
+        const int64_t r = cta_scan<4>(Q.A, Q.n, Q.B, Q.m, x, y, off,
+                                                 min((int64_t)CHUNK_BYTES, lim - off), S.smin);
+        if (r >= 0)
+            return r;
+        off += CHUNK_BYTES;
+    }
+    if (off >= lim)
+        return lim;
+    C.longs++;
     JobSlot *sl = &P.slots[blockIdx.x];
-    const uint32_t nch = (uint32_t)((lim + CHUNK_BYTES - 1) / CHUNK_BYTES);
+    const int64_t rest = lim - off;
+    const uint32_t nch = (uint32_t)((rest + CHUNK_BYTES - 1) / CHUNK_BYTES);
     const int word = blockIdx.x >> 6;
     const unsigned long long bit = 1ull << (blockIdx.x & 63);
     if (tid == 0) {
@@ -329,54 +419,42 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const
         sl->B = Q.B;
         sl->n = Q.n;
         sl->m = Q.m;
-        sl->x = x;
-        sl->y = y;
-        sl->lim = lim;
-        sl->result = (unsigned long long)lim;
+        sl->x = x + off;
+        sl->y = y + off;
+        sl->lim = rest;
+        sl->result = (unsigned long long)rest;
         sl->done = 0;
         sl->nchunks = nch;
         const uint32_t jid = (uint32_t)(sl->claim >> 32) + 1u;
         __threadfence();
         atomicExch(&sl->claim, ((unsigned long long)(jid ? jid : 1u) << 32));
-        if (nch > 1)
-            atomicOr(&P.ctl->active[word], bit);
+        atomicOr(&P.ctl->active[word], bit);
     }
     __syncthreads();
     for (;;) {
         if (tid == 0) {
-            int64_t c;
-            while ((c = try_claim(sl)) == -2) {
-            }
-            S.bcl[1] = c;
+            const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
+            const uint32_t cnt = (uint32_t)w0;
+            S.bcl[1] = (cnt >= nch || (unsigned long long)cnt * CHUNK_BYTES >=
+                                         *(volatile unsigned long long *)&sl->result)
+                           ? -1
+                           : claim_chunk(sl);
         }
         __syncthreads();
         const int64_t c = S.bcl[1];
         __syncthreads();
         if (c < 0)
             break;
-        scan_chunk(S, sl, c);
+        serve_claim(S, sl, c);
     }
     if (tid == 0) {
-        if (nch > 1)
-            atomicAnd(&P.ctl->active[word], ~bit);
-        unsigned long long w = ld_acquire_u64(&sl->claim);
-        uint32_t nclaimed = 0;
-        for (;;) {
-            nclaimed = (uint32_t)w;
-            if (nclaimed == CLAIM_CLOSED) { // not reachable: only the owner closes
-                nclaimed = 0;
-                break;
-            }
-            const unsigned long long nw = (w & 0xffffffff00000000ull) | CLAIM_CLOSED;
-            const unsigned long long old = atomicCAS(&sl->claim, w, nw);
-            if (old == w)
-                break;
-            w = old;
-        }
+        atomicAnd(&P.ctl->active[word], ~bit);
+        const unsigned long long w = atomicAdd(&sl->claim, (unsigned long long)CLAIM_CLOSE);
+        const uint32_t nvalid = (uint32_t)w; // claims made before the close
         const uint64_t t0 = gtimer();
-        while (*(volatile unsigned int *)&sl->done < nclaimed) {
+        while (*(volatile unsigned int *)&sl->done < nvalid) {
             if (gtimer() - t0 > P.spin_ns) {
-                wait_failed(P, 1, 0, nclaimed, *(volatile unsigned int *)&sl->done, 0, 0);
+                wait_failed(P, 1, 0, nvalid, *(volatile unsigned int *)&sl->done, 0, 0);
                 break;
             }
         }
@@ -386,7 +464,7 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const
     __syncthreads();
     const int64_t r = S.bcl[1];
     __syncthreads();
-    return r;
+    return off + r;
 }
 
 // ------------------------------------------------------------------ group
@@ -441,9 +519,8 @@ __device__ bool group_sync(const LvArgs &P, GroupCtl *gc, int G, const Smem &S)
 size_t lv_tiles_smem_bytes(int smax, int h)
 {
     (void)h;
-    const int lcap = 512;
-    return 128 + (size_t)lcap * (2 * sizeof(int64_t) + 2 * sizeof(int32_t)) +
-           2 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2);
+    // two frontier buffers and the open-slide list, each smax + 2*HMAX + 2
+    return 128 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2);
 }
 
 __device__ Smem carve(const LvArgs &P)
@@ -456,18 +533,14 @@ __device__ Smem carve(const LvArgs &P)
     S.n1 = reinterpret_cast<int *>(p + 64);
     S.bc = S.n1 + 4;
     p += 128;
-    S.lcap = 512;
-    S.lpos = reinterpret_cast<int64_t *>(p);
-    p += sizeof(int64_t) * S.lcap;
-    S.llim = reinterpret_cast<int64_t *>(p);
-    p += sizeof(int64_t) * S.lcap;
+    S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
-    p += sizeof(int32_t) * S.lcap;
-    S.lc = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * S.lcap;
     S.F[0] = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (P.smax + 2 * HMAX + 2);
     S.F[1] = reinterpret_cast<int32_t *>(p);
+    S.err = &P.ctl->error;
+    S.diag = P.ctl->diag;
     return S;
 }
 
@@ -500,11 +573,80 @@ __device__ __forceinline__ int32_t *halo_ptr(const LvArgs &P, int cta, int parit
     return P.halo + ((int64_t)(cta * 2 + parity) * 2 + side) * HMAX;
 }
 
+// The slide of open diagonal d: its start row c and the bound lim_abs of
+// its first mismatch (the string end, or the hash answer + 1).
+__device__ __forceinline__ void open_bounds(const LvArgs &P, const Pair &Q, const int32_t *prev, int64_t off,
+                                            int64_t tau, int64_t d, int64_t *c, int64_t *lim_abs, Counters &C,
+                                            bool own)
+{
+    const int64_t cc = start_row(prev, off, d, tau, Q.n, Q.m);
+    const int64_t full = min(Q.n - cc, Q.m - cc - d);
+    int64_t lim = full;
+    if (Q.hash && full > 0) {
+        const int64_t h = hash_lcp(P.pow2, Q.TA, Q.TB, cc, cc + d, 0, full);
+        C.hashq += own;
+        lim = min(h + 1, full);
+    }
+    *c = cc;
+    *lim_abs = cc + lim;
+}
+
+// Open slides of one round: one warp each (t2_cap bytes, which finishes
+// most of them in one or two 2 KiB steps); what is still open after that
+// goes to the whole CTA and, if longer still, to the job slots
+// (long_slide).  The per-thread bytes already compared are simply compared
+// again (at most t1_cap).
+__device__ __noinline__ void open_slides(const LvArgs &P, const Smem &S, const Pair &Q, const int32_t *prev,
+                                         int32_t *cur, int64_t off, int64_t tau, int64_t a, int64_t b, int n1,
+                                         Counters &C)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    {
+        for (int j = warp; j < n1; j += nw) {
+            const int64_t d = S.ld[j];
+            const bool own = d >= a && d < b;
+            int64_t c = 0, lim = 0;
+            if (lane == 0)
+                open_bounds(P, Q, prev, off, tau, d, &c, &lim, C, own);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            lim = __shfl_sync(0xffffffffu, lim, 0);
+            bool open;
+            const int64_t l = slide_warp(Q.A, Q.n, Q.B, Q.m, c, c + d, 0, lim - c, P.t2_cap, &open);
+            if (lane == 0) {
+                if (!open) {
+                    cur[d - off] = (int32_t)finish_slide(Q, c, d, c + l, lim, own, C);
+                    S.ld[j] = INT32_MIN; // finished
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = 0; j < n1; j++) {
+        const int64_t d = S.ld[j];
+        if (d == INT32_MIN)
+            continue;
+        const bool own = d >= a && d < b;
+        if (tid == 0) {
+            int64_t c, lim;
+            open_bounds(P, Q, prev, off, tau, d, &c, &lim, C, own);
+            S.bcl[2] = c;
+            S.bcl[3] = lim;
+        }
+        __syncthreads();
+        const int64_t c = S.bcl[2], lim = S.bcl[3];
+        __syncthreads();
+        const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c, C);
+        if (tid == 0)
+            cur[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
+    }
+    __syncthreads();
+}
+
 // Runs one pair on the group.  Returns false if the launch must stop.
 __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, GroupCtl *gc, int gi, int G,
                          int c0, int32_t *gfb, unsigned long long iter, Counters &C)
 {
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int h = P.h;
     Pair Q;
     Q.A = D.A;
@@ -592,7 +734,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         }
         if ((t + h - 1 > R) && (R < nm)) {
             // ------------------------------------------ epoch change
-            const uint64_t te0 = gtimer();
+            const uint64_t te0 = clock64();
             const int64_t Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
             if (t + h - 1 > Rn && Rn < nm) {
                 if (tid == 0)
@@ -631,7 +773,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
                     dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? ld_cg(buf + d + P.kcap + 2) : NEG;
             }
             __syncthreads();
-            C.tm[3] += gtimer() - te0;
+            C.tm[3] += clock64() - te0;
             if (!T.has)
                 continue;
         }
@@ -639,88 +781,45 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         const int64_t a = T.a, b = T.b, off = a - h - 1; // smem index = d - off
         bool fin = false;
         for (int r = 0; r < h && !fin; r++) {
-            const uint64_t tr0 = gtimer();
+            const uint64_t tr0 = clock64();
             const int64_t tau = t + r;
             const int64_t ra = a - h + 1 + r, rb = b + h - 1 - r; // computed range [ra, rb)
             const int64_t blo = max(-tau, -n), bhi = min(tau, m);
-            const int32_t *prev = S.F[(tau - 1) & 1];
             int32_t *cur = S.F[tau & 1];
             // outside the band: minus infinity
             for (int64_t d = ra + tid; d < rb; d += nt)
                 if (d < blo || d > bhi)
                     cur[d - off] = NEG;
-            const int64_t lo = max(ra, blo), hi = min(rb - 1, bhi);
-            phase_a(
-                P, Q, lo, hi,
-                [&](int64_t d) -> int64_t {
-                    if (tau == 0)
-                        return 0;
-                    const int64_t x1 = prev[d - 1 - off];
-                    const int64_t x2 = (int64_t)prev[d - off] + 1;
-                    const int64_t x3 = (int64_t)prev[d + 1 - off] + 1;
-                    return min(max(x1, max(x2, x3)), min(n, m - d));
-                },
-                [&](int64_t d, int64_t c, int64_t l, int64_t full) {
-                    cur[d - off] = (int32_t)(c + l);
-                    if (d >= a && d < b) {
-                        C.slide += l;
-                        C.mism += (l < full);
-                    }
-                },
-                [&](int64_t d, int64_t c, int64_t pos, int64_t lim) {
-                    const int s = atomicAdd(S.n1, 1);
-                    if (s < S.lcap) {
-                        S.ld[s] = (int32_t)d;
-                        S.lc[s] = (int32_t)c;
-                        S.lpos[s] = pos;
-                        S.llim[s] = lim;
-                    } else {
-                        bool o;
-                        const int64_t p = pos + slide_thread(Q.A, n, Q.B, m, pos, pos + d, lim - pos,
-                                                             INT64_MAX, &o);
-                        cur[d - off] = (int32_t)finish_slide(Q, c, d, p, lim, d >= a && d < b, C);
-                    }
-                },
-                C);
+            RoundArgs RA;
+            RA.A = Q.A;
+            RA.B = Q.B;
+            RA.n = n;
+            RA.m = m;
+            RA.prev = S.F[(tau - 1) & 1];
+            RA.cur = cur;
+            RA.off = off;
+            RA.lo = max(ra, blo);
+            RA.hi = min(rb - 1, bhi);
+            RA.tau = tau;
+            RA.a = a;
+            RA.b = b;
+            RA.t1_cap = P.t1_cap;
+            RA.n1 = S.n1;
+            RA.open = S.ld;
+            RA.err = &P.ctl->error;
+            RA.diag = P.ctl->diag;
+            const RoundCount rc = tile_round(RA);
+            C.slide += rc.slide;
+            C.mism += rc.mism;
             __syncthreads();
-            const uint64_t tr1 = gtimer();
+            const uint64_t tr1 = clock64();
             C.tm[0] += tr1 - tr0;
-            const int n1 = min(*S.n1, S.lcap);
+            const int n1 = *S.n1;
             if (n1 > 0) {
-                // one warp per open slide
-                for (int j = warp; j < n1; j += nw) {
-                    const int64_t d = S.ld[j], c = S.lc[j], pos = S.lpos[j], lim = S.llim[j];
-                    bool open;
-                    const int64_t l =
-                        slide_warp(Q.A, n, Q.B, m, pos, pos + d, 0, lim - pos, P.t2_cap, &open);
-                    if (lane == 0) {
-                        if (!open) {
-                            cur[d - off] = (int32_t)finish_slide(Q, c, d, pos + l, lim, d >= a && d < b, C);
-                            S.llim[j] = -1; // finished
-                        } else {
-                            S.lpos[j] = pos + l;
-                        }
-                    }
-                }
-                __syncthreads();
-                // still open: a job for the whole CTA, helped by waiting CTAs
-                for (int j = 0; j < n1; j++) {
-                    const int64_t lim = S.llim[j];
-                    if (lim < 0)
-                        continue;
-                    const int64_t d = S.ld[j], pos = S.lpos[j];
-                    const int64_t rr = long_slide(P, S, Q, pos, pos + d, lim - pos);
-                    if (tid == 0) {
-                        const int64_t c = S.lc[j];
-                        const bool own = d >= a && d < b;
-                        cur[d - off] = (int32_t)finish_slide(Q, c, d, pos + rr, lim, own, C);
-                        C.longs += own;
-                    }
-                }
-                __syncthreads();
+                open_slides(P, S, Q, S.F[(tau - 1) & 1], cur, off, tau, a, b, n1, C);
                 if (tid == 0)
                     *S.n1 = 0;
-                C.tm[1] += gtimer() - tr1;
+                C.tm[1] += clock64() - tr1;
             }
             // termination: the tile owning the target diagonal reports k
             if (target >= a && target < b && target >= blo && target <= bhi && cur[target - off] == n) {
@@ -742,7 +841,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         t += h;
         C.blocks++;
         // ---------------------------------------------- halo exchange
-        const uint64_t tw0 = gtimer();
+        const uint64_t tw0 = clock64();
         const int parity = (int)((t / h) & 1);
         const int32_t *last = S.F[(t - 1) & 1];
         int32_t *hl = halo_ptr(P, blockIdx.x, parity, 0), *hr = halo_ptr(P, blockIdx.x, parity, 1);
@@ -794,7 +893,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             edge[b + tid - off] = T.right >= 0 ? ld_cg(halo_ptr(P, T.right, parity, 0) + tid) : NEG;
         }
         __syncthreads();
-        C.tm[2] += gtimer() - tw0;
+        C.tm[2] += clock64() - tw0;
     }
 }
 
@@ -809,12 +908,19 @@ __device__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
         if (v[1]) atomicAdd(&D.res[R_MISMATCH], v[1]);
         if (v[2]) atomicAdd(&D.res[R_HASHQ], v[2]);
         if (v[3]) atomicAdd(&D.res[R_HASHCOLL], v[3]);
-        if (v[4]) atomicAdd(&D.res[R_LONG], v[4]);
     }
-    if (first_cta && threadIdx.x == 0) {
-        D.res[R_WIDE] = C.blocks;
+    if (threadIdx.x == 0) {
+        // counted once per CTA (the values are the CTA's, not per thread)
+        if (C.longs)
+            atomicAdd(&D.res[R_LONG], C.longs);
+        if (first_cta)
+            D.res[R_WIDE] = C.blocks;
+        // phase cycles: the largest over the group's CTAs, and the sum of
+        // round + slide cycles (for the average busy time)
         for (int i = 0; i < 4; i++)
-            D.res[R_T0 + i] = C.tm[i];
+            atomicMax(&D.res[R_T0 + i], C.tm[i]);
+        atomicAdd(&D.res[R_T0 + 4], C.tm[0] + C.tm[1]);
+        atomicAdd(&D.res[R_T0 + 5], 1ull);
     }
     C = Counters();
 }
@@ -910,29 +1016,34 @@ __global__ void lcp_query_kernel(const uint8_t *A, int64_t n, const uint8_t *B, 
     }
 }
 
-// Method 2: each CTA claims chunks of the queries' slots (published by the
-// host, claim = (1 << 32)) until none is left; the results stay in slots.
+// Method 2: every CTA claims chunks of the queries' slots (published by the
+// host: claim = 1 << 32, result = lim) until each slot is exhausted; the
+// answers stay in the slots.
 __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots)
 {
     __shared__ unsigned long long s_min;
     __shared__ long long s_c;
+    __shared__ int s_bc[8];
     Smem S{};
     S.smin = &s_min;
+    S.bc = s_bc;
     for (int j = 0; j < nslots; j++) {
         JobSlot *sl = &slots[(j + blockIdx.x) % nslots];
         for (;;) {
             if (threadIdx.x == 0) {
-                int64_t c;
-                while ((c = try_claim(sl)) == -2) {
-                }
-                s_c = c;
+                const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
+                const uint32_t cnt = (uint32_t)w0;
+                s_c = (cnt >= *(volatile unsigned int *)&sl->nchunks ||
+                       (unsigned long long)cnt * CHUNK_BYTES >= *(volatile unsigned long long *)&sl->result)
+                          ? -1
+                          : claim_chunk(sl);
             }
             __syncthreads();
             const int64_t c = s_c;
             __syncthreads();
             if (c < 0)
                 break;
-            scan_chunk(S, sl, c);
+            serve_claim(S, sl, c);
         }
     }
 }
