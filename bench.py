@@ -290,8 +290,9 @@ def run_single(args, D: Dist):
                    "parallelism": f"replicas x{D.ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                     "kernel": "lv_single_kernel",
-                     "traffic": profile_traffic(f"lv_single_{args.workload}.md"),
+                     "kernel": "lv_tiles_kernel",
+                     "traffic": profile_traffic(f"lv_tiles_{args.workload}.md")
+                     if args.lcp == "direct" and args.ks == "10,1000,100000" and not args.n else None,
                      "algorithmic_bytes_per_launch": cbytes / max(1, len(recs))},
         "e2e": {"value": D.sum(e_ext) / e2e_s, "unit": "ext/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": 8 * len(pairs) * 8},
