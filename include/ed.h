@@ -170,6 +170,30 @@ int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T,
 /* The hash base p used by the context (derived from hash_seed). */
 uint64_t ed_hash_base(ed_ctx *ctx);
 
+/* Largest len accepted by ed_prefix_hash_noalloc (21843 scan tiles of 4096
+ * bytes: the scan's 48-byte look-back descriptors plus a 64-byte header fit
+ * its 1 MiB scratch array). */
+#define ED_NOALLOC_MAX_LEN ((size_t)89468928)
+
+/* ed_prefix_hash_dev for callers that cannot allocate device memory: code
+ * embedded in a host framework whose memory manager owns every device
+ * allocation (a stray cudaMalloc escapes its budget and accounting, or is
+ * refused), and code that cannot afford cudaMalloc / cudaFree on its path
+ * (cudaFree waits for the whole device).  No context is needed and nothing
+ * is allocated: the scan's working state lives in a
+ * fixed 1 MiB array compiled into the library, which every GPU that loads
+ * the library keeps until the process exits.  The paper has no counterpart;
+ * the table computed is the same as ed_prefix_hash_dev's with the given
+ * base.  X and T are device pointers (T: len + 1 uint64 entries); base must
+ * lie in [2, 2^61-2].  len above ED_NOALLOC_MAX_LEN returns ED_EINVAL.  The
+ * first call on a device looks up the array's device address (make that
+ * call before any stream capture).  Every call shares the array and clears
+ * it on `stream` before use: calls whose work overlaps on the GPU (two
+ * streams, or two threads) race and must be serialised by the caller.
+ * Synchronous on `stream` (NULL = legacy default). */
+int ed_prefix_hash_noalloc(const uint8_t *X, size_t len, uint64_t base, uint64_t *T,
+                           void *stream);
+
 /* Runs Algorithm 1 on DEVICE strings for rounds 0..t_max and writes the
  * frontiers to the HOST array out[t * (2*t_max+1) + (d + t_max)] (int32;
  * INT32 value -1061109568 where undefined).  *k receives the distance if

@@ -84,6 +84,7 @@ _SIGS = {
     "ed_prefix_hash_dev": (_I, [_P, _P, _S, _P, _P]),
     "ed_hash_base": (_U64, [_P]),
     "ed_frontiers_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _P, _P]),
+    "ed_prefix_hash_noalloc": (_I, [_P, _S, _U64, _P, _P]),
 }
 
 
@@ -291,6 +292,19 @@ def ed_prefix_hash_dev(ctx, X, stream=None):
 
 def ed_hash_base(ctx) -> int:
     return int(load().ed_hash_base(ctx))
+
+
+ED_NOALLOC_MAX_LEN = 89468928
+
+
+def ed_prefix_hash_noalloc(X, base: int, T, stream=None) -> None:
+    """The prefix table of X into the caller's CUDA tensor T (int64, len+1
+    entries) without any allocation by the library (include/ed.h)."""
+    px, n = _dev_buf(X)
+    if T.numel() != n + 1 or not T.is_cuda or T.element_size() != 8:
+        raise ValueError("T must be a CUDA tensor of len(X) + 1 8-byte entries")
+    _check(None, load().ed_prefix_hash_noalloc(px, n, base, T.data_ptr(), _stream_ptr(stream)),
+           "ed_prefix_hash_noalloc")
 
 
 def ed_frontiers_dev(ctx, A, B, t_max: int, stream=None):

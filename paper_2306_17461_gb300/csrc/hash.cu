@@ -176,3 +176,61 @@ cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base,
 }
 
 } // namespace edg
+
+// ---------------------------------------------------------------------------
+// Allocation-free prefix hash (see ed_prefix_hash_noalloc in include/ed.h).
+//
+// The scan's look-back descriptors live in this file-scope device array
+// instead of memory the caller or a context allocates.  Every GPU that loads
+// the library holds it until the process exits.  Host code only ever uses
+// the array's device address, obtained once per device with
+// cudaGetSymbolAddress (the name itself is a host-side stand-in).
+#include <mutex>
+
+#include "../../include/ed.h"
+
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 1u << 20; // 1 MiB
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scan[NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+} // namespace
+
+extern "C" int ed_prefix_hash_noalloc(const uint8_t *X, size_t len, uint64_t base, uint64_t *T,
+                                      void *stream)
+{
+    if (!T || (len && !X) || base < 2 || base >= ((1ull << 61) - 1))
+        return ED_EINVAL;
+    const size_t need = edg::prefix_hash_state_bytes((int64_t)len);
+    if (len > (size_t)INT64_MAX || need > NOALLOC_SCRATCH_BYTES)
+        return ED_EINVAL; // beyond the fixed scratch: at most ED_NOALLOC_MAX_LEN bytes
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES)
+        return ED_ECUDA;
+    void *scratch = nullptr;
+    {
+        // first call on this device: look up the array's device address
+        std::lock_guard<std::mutex> g(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scan) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return ED_ECUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        scratch = g_noalloc_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // the look-back descriptors must start at zero: cleared on every call
+    if (edg::launch_prefix_hash(X, (int64_t)len, base, T, scratch, need, s) != cudaSuccess)
+        return ED_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess)
+        return ED_ECUDA;
+    return ED_OK;
+}
