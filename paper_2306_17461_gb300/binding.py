@@ -114,7 +114,7 @@ def _strerror(code: int) -> str:
 def _check(ctx, code: int, what: str):
     if code < 0:
         detail = ""
-        if ctx is not None and code in (ED_ECUDA, ED_ETIMEOUT):
+        if ctx is not None and code in (ED_ECUDA, ED_ETIMEOUT, ED_ELIMIT):
             detail = load().ed_last_cuda_error(ctx).decode()
         raise EdError(code, what, detail)
     return code

@@ -119,6 +119,8 @@ struct TileJob {
     const uint64_t *TA, *TB;
     int32_t *dump;
     int64_t dump_tmax;
+    int G;       // CTAs of the group the pair runs on (1 .. grid)
+    double cost; // estimated run time (any unit), to share CTAs among classes
 };
 
 } // namespace
@@ -256,19 +258,70 @@ int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB
     return ED_OK;
 }
 
-// Runs pairs on the tile kernel: groups of group_size CTAs claim pairs from
-// a queue.  k[i] receives each distance; per-pair counters are summed into
-// ctx->last.
-int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cudaStream_t s,
-              std::vector<uint64_t> &k)
+// One tile launch over the jobs, CTA groups by class (one class per group
+// size wanted).  Every class that fits gets one group, largest first; the
+// remaining CTAs go, one group at a time, to the class whose estimated run
+// time per group is highest.  k[i] and st[i] receive each pair's distance
+// and status (0, ST_WIDE, ST_LIMIT); the counters of finished pairs are
+// summed into ctx->last.
+static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s,
+                          std::vector<uint64_t> &k, std::vector<uint32_t> &st)
 {
     int r;
     const int np = (int)jobs.size();
-    const int G = std::max(1, std::min(group_size, ctx->grid));
-    const int ngroups = std::max(1, ctx->grid / G);
-    const int grid = ngroups * G;
     const int h = ctx->cfg.block_rounds > 0 ? std::min(ctx->cfg.block_rounds, HMAX) : HMAX;
     const int s0 = ctx->cfg.tile_width > 0 ? ctx->cfg.tile_width : 64;
+    // classes, ascending group size; pairs by class, then cost, largest first
+    std::vector<int> sizes;
+    for (const TileJob &j : jobs)
+        sizes.push_back(std::max(1, std::min(j.G, ctx->grid)));
+    std::vector<int> Gs = sizes;
+    std::sort(Gs.begin(), Gs.end());
+    Gs.erase(std::unique(Gs.begin(), Gs.end()), Gs.end());
+    if ((int)Gs.size() > MAX_CLS) { // merge the smallest classes upwards
+        const int drop = (int)Gs.size() - MAX_CLS;
+        for (int &g : sizes)
+            if (g < Gs[drop])
+                g = Gs[drop];
+        Gs.erase(Gs.begin(), Gs.begin() + drop);
+    }
+    const int ncls = (int)Gs.size();
+    auto cls_of = [&](int g) { return (int)(std::lower_bound(Gs.begin(), Gs.end(), g) - Gs.begin()); };
+    std::vector<int> ord(np);
+    for (int i = 0; i < np; i++)
+        ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
+        const int ca = cls_of(sizes[a]), cb = cls_of(sizes[b]);
+        return ca != cb ? ca < cb : jobs[a].cost > jobs[b].cost;
+    });
+    std::vector<int> npc(ncls, 0), ng(ncls, 0);
+    std::vector<double> wc(ncls, 0.0);
+    std::vector<int64_t> nmc(ncls, 0);
+    for (int i = 0; i < np; i++) {
+        const int c = cls_of(sizes[i]);
+        npc[c]++;
+        wc[c] += std::max(jobs[i].cost, 1.0);
+        nmc[c] = std::max(nmc[c], std::max(jobs[i].n, jobs[i].m));
+    }
+    int used = 0;
+    for (int c = ncls - 1; c >= 0; c--)
+        if (used + Gs[c] <= ctx->grid) {
+            ng[c] = 1;
+            used += Gs[c];
+        }
+    for (;;) {
+        int best = -1;
+        double bw = -1.0;
+        for (int c = 0; c < ncls; c++)
+            if (ng[c] > 0 && ng[c] < npc[c] && used + Gs[c] <= ctx->grid && wc[c] / ng[c] > bw) {
+                bw = wc[c] / ng[c];
+                best = c;
+            }
+        if (best < 0)
+            break;
+        ng[best]++;
+        used += Gs[best];
+    }
     int64_t nm = 0;
     for (const TileJob &j : jobs)
         nm = std::max(nm, std::max(j.n, j.m));
@@ -277,10 +330,37 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
         kcap = std::min<int64_t>(kcap, ctx->cfg.max_rounds);
     kcap = std::min<int64_t>(kcap, (int64_t)1 << 28);
     kcap = std::max<int64_t>(kcap, h);
-    const int64_t smax = std::max<int64_t>(
-        std::max<int64_t>(h, s0), std::min<int64_t>(SMAX_LIMIT, (2 * std::min(kcap, nm) + 1 + G - 1) / G + 1));
-    const int64_t gstride = 2 * kcap + 5;
-    if ((r = ensure(ctx, ctx->gf, sizeof(int32_t) * (size_t)(2 * gstride) * ngroups)) != ED_OK ||
+    // tile capacity: what the widest band of any class needs, at most SMAX_LIMIT
+    // (a group also runs pairs of the classes below its own)
+    int64_t smax = std::max(h, s0), nm_below = 0;
+    for (int c = 0; c < ncls; c++) {
+        nm_below = std::max(nm_below, nmc[c]);
+        if (ng[c] > 0)
+            smax = std::max<int64_t>(
+                smax, std::min<int64_t>(SMAX_LIMIT, (2 * std::min(kcap, nm_below) + 1 + Gs[c] - 1) / Gs[c] + 1));
+    }
+    LvArgs P{};
+    int ngroups = 0;
+    int64_t gf_total = 0;
+    int cta = 0;
+    int pi = 0;
+    for (int c = 0; c < ncls; c++) {
+        P.cls_G[c] = Gs[c];
+        P.cls_c0[c] = cta;
+        P.cls_g0[c] = ngroups;
+        P.cls_p0[c] = pi;
+        P.cls_kc[c] = (int32_t)std::min<int64_t>(kcap, (int64_t)Gs[c] * smax);
+        P.cls_gf[c] = gf_total;
+        cta += ng[c] * Gs[c];
+        ngroups += ng[c];
+        pi += npc[c];
+        gf_total += (int64_t)ng[c] * 2 * (2 * (int64_t)P.cls_kc[c] + 5);
+    }
+    P.cls_c0[ncls] = cta;
+    P.cls_p0[ncls] = pi;
+    P.ncls = ncls;
+    const int grid = cta;
+    if ((r = ensure(ctx, ctx->gf, sizeof(int32_t) * (size_t)std::max<int64_t>(gf_total, 1))) != ED_OK ||
         (r = ensure(ctx, ctx->ctl, sizeof(LaunchCtl))) != ED_OK ||
         (r = ensure(ctx, ctx->gctl, sizeof(GroupCtl) * ngroups)) != ED_OK ||
         (r = ensure(ctx, ctx->slots, sizeof(JobSlot) * grid)) != ED_OK ||
@@ -297,29 +377,28 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
         CK(cudaMallocHost((void **)&ctx->h_res, hres));
         ctx->h_res_cap = hres;
     }
+    // pair slot q runs job ord[q]; its counters land in row q
     std::vector<PairDesc> pd(np);
-    for (int i = 0; i < np; i++) {
-        pd[i] = PairDesc{};
-        pd[i].A = jobs[i].A;
-        pd[i].B = jobs[i].B;
-        pd[i].n = jobs[i].n;
-        pd[i].m = jobs[i].m;
-        pd[i].TA = jobs[i].TA;
-        pd[i].TB = jobs[i].TB;
-        pd[i].res = (unsigned long long *)ctx->res.p + (size_t)R_COUNT * i;
-        pd[i].dump = jobs[i].dump;
-        pd[i].dump_tmax = (int32_t)jobs[i].dump_tmax;
+    for (int q = 0; q < np; q++) {
+        const TileJob &j = jobs[ord[q]];
+        pd[q] = PairDesc{};
+        pd[q].A = j.A;
+        pd[q].B = j.B;
+        pd[q].n = j.n;
+        pd[q].m = j.m;
+        pd[q].TA = j.TA;
+        pd[q].TB = j.TB;
+        pd[q].res = (unsigned long long *)ctx->res.p + (size_t)R_COUNT * q;
+        pd[q].dump = j.dump;
+        pd[q].dump_tmax = (int32_t)j.dump_tmax;
     }
-    LvArgs P{};
     P.pairs = (const PairDesc *)ctx->pdesc.p;
     P.npairs = np;
-    P.group_size = G;
     P.gctl = (GroupCtl *)ctx->gctl.p;
     P.ctl = (LaunchCtl *)ctx->ctl.p;
     P.slots = (JobSlot *)ctx->slots.p;
     P.halo = (int32_t *)ctx->halo.p;
     P.gf = (int32_t *)ctx->gf.p;
-    P.gf_stride = 2 * gstride;
     P.kcap = (int32_t)kcap;
     P.smax = (int32_t)smax;
     P.h = h;
@@ -347,19 +426,24 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->last.kernel_ms += ms;
-    const int st = status_from_kernel(*(uint32_t *)(ctx->h_res + (size_t)R_COUNT * np));
-    if (st != ED_OK) {
+    const int lst = status_from_kernel(*(uint32_t *)(ctx->h_res + (size_t)R_COUNT * np));
+    if (lst != ED_OK) {
         unsigned long long dg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         cudaMemcpy(dg, (char *)ctx->ctl.p + offsetof(LaunchCtl, diag), sizeof(dg), cudaMemcpyDeviceToHost);
         char buf[256];
         std::snprintf(buf, sizeof(buf), "kernel check failed: site %llu cta %llu t %llu want %llx seen %llx %llx %llx",
                       dg[0], dg[1], dg[2], dg[3], dg[4], dg[5], dg[6]);
         ctx->last_err = buf;
-        return st;
+        return lst;
     }
-    k.resize(np);
-    for (int i = 0; i < np; i++) {
-        const unsigned long long *R = ctx->h_res + (size_t)R_COUNT * i;
+    k.assign(np, 0);
+    st.assign(np, 0);
+    for (int q = 0; q < np; q++) {
+        const int i = ord[q];
+        const unsigned long long *R = ctx->h_res + (size_t)R_COUNT * q;
+        st[i] = (uint32_t)R[R_STATUS];
+        if (st[i] != 0)
+            continue;
         k[i] = R[R_K];
         ctx->last.extensions += count_extensions(jobs[i].n, jobs[i].m, (int64_t)R[R_K]);
         ctx->last.slide_chars += R[R_SLIDE];
@@ -378,12 +462,54 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, int group_size, cud
     return ED_OK;
 }
 
+// Runs pairs on the tile kernel until each has its distance: a pair whose
+// band outgrew its group runs again on a group twice as large; a pair
+// that needs more than the whole grid, or more rounds than the cap, fails
+// the call with ED_ELIMIT.
+int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s, std::vector<uint64_t> &k)
+{
+    k.assign(jobs.size(), 0);
+    std::vector<TileJob> cur = jobs;
+    std::vector<size_t> idx(jobs.size());
+    for (size_t i = 0; i < idx.size(); i++)
+        idx[i] = i;
+    while (!cur.empty()) {
+        std::vector<uint64_t> kk;
+        std::vector<uint32_t> st;
+        int r = run_tiles_once(ctx, cur, s, kk, st);
+        if (r != ED_OK)
+            return r;
+        std::vector<TileJob> next;
+        std::vector<size_t> nidx;
+        for (size_t i = 0; i < cur.size(); i++) {
+            if (st[i] == 0) {
+                k[idx[i]] = kk[i];
+            } else if (st[i] == ST_WIDE && cur[i].G < ctx->grid) {
+                TileJob j = cur[i];
+                j.G = std::min(ctx->grid, 2 * std::max(1, j.G));
+                next.push_back(j);
+                nidx.push_back(idx[i]);
+            } else {
+                char buf[160];
+                std::snprintf(buf, sizeof(buf), "pair %zu: %s", idx[i],
+                              st[i] == ST_WIDE ? "band wider than the whole grid's tiles hold"
+                                               : "more rounds than the configured cap");
+                ctx->last_err = buf;
+                return ED_ELIMIT;
+            }
+        }
+        cur.swap(next);
+        idx.swap(nidx);
+    }
+    return ED_OK;
+}
+
 // One pair, device strings, on stream s (the whole grid as one group).
 int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
              cudaStream_t s, int32_t *dump, int64_t dump_tmax, uint64_t *k_out)
 {
     int r;
-    TileJob j{dA, dB, n, m, nullptr, nullptr, dump, dump_tmax};
+    TileJob j{dA, dB, n, m, nullptr, nullptr, dump, dump_tmax, ctx->grid, 1.0};
     if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
         CK(cudaEventRecord(ctx->ev2, s));
         if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
@@ -392,7 +518,7 @@ int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64
         j.TB = (const uint64_t *)ctx->hashB.p;
     }
     std::vector<uint64_t> k;
-    if ((r = run_tiles(ctx, {j}, ctx->grid, s, k)) != ED_OK)
+    if ((r = run_tiles(ctx, {j}, s, k)) != ED_OK)
         return r;
     if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
         float bms = 0.f;
@@ -680,9 +806,7 @@ static int batch_launch(ed_ctx *ctx, std::vector<BatchPair> &hp, const std::vect
     Bg.t1_cap = 64;
     Bg.t2_cap = 8192;
     Bg.spin_ns = ctx->cfg.spin_limit_ns;
-    const size_t smem = lv_batch_smem_bytes(BATCH_W);
-    int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
-    occ = std::min(occ, 2048 / lv_batch_threads());
+    const int occ = lv_batch_ctas_per_sm(BATCH_W);
     CK(cudaEventRecord(ctx->ev0, s));
     CK(launch_lv_batch(Bg, ctx->num_sms * occ, s, budget_ns));
     CK(cudaEventRecord(ctx->ev1, s));
@@ -703,17 +827,48 @@ static int batch_launch(ed_ctx *ctx, std::vector<BatchPair> &hp, const std::vect
     return ED_OK;
 }
 
-// CTAs per group for pairs parked by the batch kernel: enough that the band
-// of a pair at a few percent edits fits the tiles, and no more groups than
-// pairs.
-static int parked_group_size(ed_ctx *ctx, int64_t nm_max, size_t nparked)
+// A tile job for a pair parked by the batch kernel after t rounds with its
+// furthest row at `reach`.  Its distance is estimated by extrapolating the
+// rounds per row so far (t * n / reach, between t and max(n, m)); its group
+// is the smallest power of two of CTAs whose tiles hold that band with a
+// quarter to spare.  The estimate only places the pair: one whose band
+// outgrows its group runs again on a larger group.
+static TileJob parked_job(ed_ctx *ctx, const BatchPair &b)
 {
-    int G = 4;
-    while (G < ctx->grid && (int64_t)G * SMAX_LIMIT / 4 < nm_max / 5)
-        G *= 2;
-    while (G < ctx->grid && (size_t)(ctx->grid / G) > nparked)
-        G *= 2;
-    return std::min(G, ctx->grid);
+    const int64_t nm = std::max(b.n, b.m);
+    const int64_t t = std::max<int64_t>(b.t, 1);
+    int64_t kest = b.reach > 0 ? (int64_t)((double)t * (double)b.n / (double)b.reach) : nm;
+    kest = std::min(std::max(kest, t), nm);
+    TileJob j{b.A, b.B, b.n, b.m, nullptr, nullptr, nullptr, 0, 1, (double)kest};
+    const int64_t band = std::min<int64_t>(2 * (kest + kest / 4) + 1, b.n + b.m + 1);
+    while (j.G < ctx->grid && (int64_t)j.G * SMAX_LIMIT < band)
+        j.G *= 2;
+    j.G = std::min(j.G, ctx->grid);
+    return j;
+}
+
+// While the groups the jobs ask for fill at most half of the grid, doubles
+// them: with few pairs, more CTAs per pair shorten each round.  The cost of
+// a job (for sharing CTAs among classes) is its estimated distance times
+// the round time, which grows with the band per CTA.
+static void spread_jobs(ed_ctx *ctx, std::vector<TileJob> &jobs)
+{
+    for (;;) {
+        int64_t sum = 0;
+        bool room = false;
+        for (const TileJob &j : jobs) {
+            sum += j.G;
+            room |= j.G < ctx->grid;
+        }
+        if (!room || 2 * sum > ctx->grid)
+            break;
+        for (TileJob &j : jobs)
+            j.G = std::min(ctx->grid, 2 * j.G);
+    }
+    for (TileJob &j : jobs) {
+        const double band = std::min(2.0 * j.cost + 1.0, (double)(j.n + j.m + 1));
+        j.cost = j.cost * (1.0 + band / ((double)j.G * 4096.0));
+    }
 }
 
 static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const size_t *n,
@@ -744,7 +899,6 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
         return r;
     uint64_t ext = 0, slide = 0, mism = 0;
     std::vector<size_t> parked;
-    int64_t nm_max = 0;
     for (size_t p = 0; p < np; p++) {
         const BatchPair &b = hp[p];
         if (b.state == 1) {
@@ -754,22 +908,19 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
             mism += b.mism;
         } else {
             parked.push_back(p);
-            nm_max = std::max<int64_t>(nm_max, std::max(b.n, b.m));
         }
     }
     ed_stats keep = ctx->last;
     if (!parked.empty()) {
         // pairs whose band outgrew one CTA: CTA groups of the tile kernel,
-        // largest first, all in one launch
-        std::stable_sort(parked.begin(), parked.end(),
-                         [&](size_t a, size_t b) { return std::max(n[a], m[a]) > std::max(n[b], m[b]); });
+        // sized by each pair's estimated distance, in one launch
         std::vector<TileJob> jobs;
         for (size_t p : parked)
-            jobs.push_back(TileJob{A[p], B[p], (int64_t)n[p], (int64_t)m[p], nullptr, nullptr, nullptr, 0});
+            jobs.push_back(parked_job(ctx, hp[p]));
+        spread_jobs(ctx, jobs);
         ctx->last = ed_stats{};
         std::vector<uint64_t> kk;
-        const int G = parked_group_size(ctx, nm_max, parked.size());
-        if ((r = run_tiles(ctx, jobs, G, s, kk)) != ED_OK)
+        if ((r = run_tiles(ctx, jobs, s, kk)) != ED_OK)
             return r;
         for (size_t i = 0; i < parked.size(); i++)
             k_out[parked[i]] = kk[i];
@@ -877,10 +1028,7 @@ static void engine_loop(ed_ctx *ctx)
             b.k = -1;
             order[i] = (int32_t)i;
         }
-        const size_t smem = lv_batch_smem_bytes(BATCH_W);
-        int occ = std::max(1, (int)((227 * 1024) / (smem + 1024)));
-        occ = std::min(occ, 2048 / lv_batch_threads());
-        const uint64_t grid = (uint64_t)ctx->num_sms * occ;
+        const uint64_t grid = (uint64_t)ctx->num_sms * lv_batch_ctas_per_sm(BATCH_W);
         std::rotate(order.begin(), order.begin() + (ctx->n_steps * grid) % L, order.end());
         const int rc = batch_launch(ctx, hp, order, ctx->s_pairs, ctx->s_order, ctx->s_next, ctx->sstream,
                                     2000000ull);
@@ -888,19 +1036,19 @@ static void engine_loop(ed_ctx *ctx)
         // pairs parked by the batch kernel: finish them on the tile kernel
         std::vector<size_t> parked;
         std::vector<TileJob> jobs;
-        int64_t nm_max = 0;
         if (rc == ED_OK) {
             for (size_t i = 0; i < L; i++)
                 if (hp[i].state == 2) {
                     parked.push_back(i);
-                    jobs.push_back(TileJob{hp[i].A, hp[i].B, hp[i].n, hp[i].m, nullptr, nullptr, nullptr, 0});
-                    nm_max = std::max<int64_t>(nm_max, std::max(hp[i].n, hp[i].m));
+                    jobs.push_back(parked_job(ctx, hp[i]));
                 }
         }
         std::vector<uint64_t> kk;
         int rt = ED_OK;
-        if (!jobs.empty())
-            rt = run_tiles(ctx, jobs, parked_group_size(ctx, nm_max, jobs.size()), ctx->sstream, kk);
+        if (!jobs.empty()) {
+            spread_jobs(ctx, jobs);
+            rt = run_tiles(ctx, jobs, ctx->sstream, kk);
+        }
         api.unlock();
         std::vector<Request *> still;
         for (size_t i = 0; i < L; i++) {

@@ -2,32 +2,34 @@
 //
 // Each CTA claims pairs from a work queue (atomicAdd on a head index over a
 // cost-sorted order) and runs Algorithm 1 (Sec. 3.1) on its pair with the
-// frontier in shared memory, one __syncthreads per round.  Slides escalate
-// from one thread to one warp to the whole CTA (64 KiB chunks).  A pair
-// whose band outgrows W diagonals is parked (state 2) with its frontier
-// saved, for the single-pair kernel.  With a time budget (serving), a CTA
-// stops a pair when the budget is spent, saves the round-t frontier to the
-// pair's resident buffer, and the next launch resumes it.
+// frontier in shared memory: per round, the shared round function (several
+// diagonals' loads in flight per thread), then the open slides, one warp
+// each, then the whole CTA for those still open.  A pair whose band outgrows
+// W diagonals is parked (state 2) for the tile kernel.  With a time budget
+// (serving), a CTA stops a pair at a round boundary once the budget is
+// spent, saves the round's frontier in the pair's resident buffer, and the
+// next launch resumes it.
 #include "ed_device.cuh"
 #include "lv_kernels.cuh"
+#include "lv_round.cuh"
 
 namespace edg {
 
-constexpr int BT = 256;      // threads per batch CTA
-constexpr int LB = 256;      // open-slide list entries per CTA
+constexpr int BT = 256; // threads per batch CTA
 
 struct BSmem {
-    int32_t *f[2];
-    int32_t *ld, *lc;
-    int64_t *lpos, *llim;
-    int *n1, *flag, *claim;
+    int32_t *f[2];   // frontiers, W + 3 entries each (index d + W/2 + 1)
+    int32_t *ld;     // open slides: diagonal (W + 1 entries)
+    int *n1, *flag, *claim, *reach;
+    uint32_t *err;   // self-check status of the round function
+    unsigned long long *diag;
     unsigned long long *smin;
+    long long *bcl;
 };
 
 size_t lv_batch_smem_bytes(int W)
 {
-    return 16 + 64 + (size_t)LB * (2 * sizeof(int64_t) + 2 * sizeof(int32_t)) +
-           2 * sizeof(int32_t) * ((size_t)W + 3);
+    return 256 + sizeof(int32_t) * ((size_t)W + 1) + 2 * sizeof(int32_t) * ((size_t)W + 3);
 }
 
 __device__ BSmem bcarve(int W)
@@ -36,46 +38,55 @@ __device__ BSmem bcarve(int W)
     BSmem S;
     unsigned char *p = bsmem_raw;
     S.smin = reinterpret_cast<unsigned long long *>(p);
-    p += 16;
-    S.n1 = reinterpret_cast<int *>(p);
+    S.diag = S.smin + 1;                            // 8 words
+    S.bcl = reinterpret_cast<long long *>(p + 80);  // 4 words
+    S.n1 = reinterpret_cast<int *>(p + 128);
     S.flag = S.n1 + 1;
     S.claim = S.n1 + 2;
-    p += 64;
-    S.lpos = reinterpret_cast<int64_t *>(p);
-    p += sizeof(int64_t) * LB;
-    S.llim = reinterpret_cast<int64_t *>(p);
-    p += sizeof(int64_t) * LB;
+    S.err = reinterpret_cast<uint32_t *>(S.n1 + 3);
+    S.reach = S.n1 + 4;
+    p += 256;
     S.ld = reinterpret_cast<int32_t *>(p);
-    p += sizeof(int32_t) * LB;
-    S.lc = reinterpret_cast<int32_t *>(p);
-    p += sizeof(int32_t) * LB;
+    p += sizeof(int32_t) * (W + 1);
     S.f[0] = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (W + 3);
     S.f[1] = reinterpret_cast<int32_t *>(p);
     return S;
 }
 
-// The whole CTA finishes one open slide: A[pos..lim_abs) vs B[pos+d..).
-__device__ int64_t cta_slide(const BatchPair &Pr, int64_t d, int64_t pos, int64_t lim_abs,
-                             unsigned long long *s_min)
+// The whole CTA finishes one open slide: the first mismatch of
+// A[pos..lim_abs) vs B[pos+d..), 32 KiB per step with every load in flight.
+__device__ __noinline__ int64_t cta_slide(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int64_t d,
+                                          int64_t pos, int64_t lim_abs, unsigned long long *s_min)
 {
-    for (int64_t off = 0; pos + off < lim_abs; off += CHUNK_BYTES / 4) {
-        const int64_t len = min((int64_t)CHUNK_BYTES / 4, lim_abs - pos - off);
-        const int64_t r = cta_scan<1>(Pr.A, Pr.n, Pr.B, Pr.m, pos, pos + d, off, len, s_min);
+    constexpr int64_t STEP = (int64_t)BT * 16 * 4;
+    for (int64_t off = 0; pos + off < lim_abs; off += STEP) {
+        const int64_t len = min(STEP, lim_abs - pos - off);
+        const int64_t r = cta_scan<4>(A, n, B, m, pos, pos + d, off, len, s_min);
         if (r >= 0)
             return pos + r;
     }
     return lim_abs;
 }
 
-__global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t budget_ns)
+// One warp's attempt at an open slide, out of line so that the round loop
+// keeps its registers: the first mismatch within cap bytes of the start, or
+// *open when there is none.
+__device__ __noinline__ int64_t warp_slide(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int64_t c,
+                                           int64_t d, int64_t len, int64_t cap, bool *open)
+{
+    return slide_warp(A, n, B, m, c, c + d, 0, len, cap, open);
+}
+
+__global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t budget_ns)
 {
     const BSmem S = bcarve(Bg.W);
     // 0 = no time budget; otherwise this CTA stops claiming and parks its
-    // pair once budget_ns have passed since it started
+    // pair once budget_ns have passed since it started (thread 0 decides)
     const uint64_t deadline_ns = budget_ns ? gtimer() + budget_ns : 0;
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     const int H = Bg.W / 2;
+    const int64_t off = -(int64_t)H - 1; // smem index = d - off
     for (;;) {
         if (tid == 0) {
             int c = -1;
@@ -86,6 +97,8 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
             }
             *S.claim = c;
             *S.n1 = 0;
+            *S.err = 0;
+            *S.reach = 0;
         }
         __syncthreads();
         const int pi = *S.claim;
@@ -95,6 +108,7 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
         BatchPair &Pr = Bg.pairs[pi];
         if (Pr.state != 0) // finished or parked: nothing to do
             continue;
+        const uint8_t *A = Pr.A, *B = Pr.B;
         const int64_t n = Pr.n, m = Pr.m, target = m - n;
         // restore the resident frontier (round t0) or start at round 0
         const int64_t t0 = Pr.t;
@@ -112,7 +126,7 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
         __syncthreads();
         unsigned long long slide = 0, mism = 0;
         int64_t t = t0 + 1;
-        int outcome = 0; // 0 budget spent, 1 done, 2 band too wide
+        int outcome = 0; // 0 budget spent, 1 done, 2 band too wide, 3 self-check failed
         int rounds_here = 0;
         for (;; t++) {
             const int64_t lo = max(-t, -n), hi = min(t, m);
@@ -135,90 +149,69 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
             rounds_here++;
             const int32_t *prev = S.f[(t - 1) & 1];
             int32_t *cur = S.f[t & 1];
-            for (int64_t d = lo + tid; d <= hi; d += nt) {
-                int64_t c;
-                if (t == 0) {
-                    c = 0;
-                } else {
-                    const int64_t a = prev[d + H + 1 - 1];
-                    const int64_t b = (int64_t)prev[d + H + 1] + 1;
-                    const int64_t e = (int64_t)prev[d + H + 1 + 1] + 1;
-                    c = max(a, max(b, e));
-                    c = min(c, min(n, m - d));
-                }
-                if (c < 0 || c + d < 0) {
-                    // a start row outside the grid: record it, never load it
-                    Pr.check[0] = t;
-                    Pr.check[1] = d;
-                    Pr.check[2] = c;
-                    Pr.state = 3;
-                    cur[d + H + 1] = NEG;
-                    continue;
-                }
-                const int64_t full = min(n - c, m - c - d);
-                bool open;
-                const int64_t l = slide_thread(Pr.A, n, Pr.B, m, c, c + d, full, Bg.t1_cap, &open);
-                if (!open) {
-                    cur[d + H + 1] = (int32_t)(c + l);
-                    slide += l;
-                    mism += (l < full);
-                } else {
-                    const int s = atomicAdd(S.n1, 1);
-                    if (s < LB) {
-                        S.ld[s] = (int32_t)d;
-                        S.lc[s] = (int32_t)c;
-                        S.lpos[s] = c + l;
-                        S.llim[s] = c + full;
-                    } else {
-                        bool o2;
-                        const int64_t l2 =
-                            slide_thread(Pr.A, n, Pr.B, m, c, c + d, full, INT64_MAX, &o2);
-                        cur[d + H + 1] = (int32_t)(c + l2);
-                        slide += l2;
-                        mism += (l2 < full);
-                    }
-                }
-            }
+            RoundArgs RA;
+            RA.A = A;
+            RA.B = B;
+            RA.n = n;
+            RA.m = m;
+            RA.prev = prev;
+            RA.cur = cur;
+            RA.off = off;
+            RA.lo = lo;
+            RA.hi = hi;
+            RA.tau = t;
+            RA.a = lo;
+            RA.b = hi + 1;
+            RA.t1_cap = Bg.t1_cap;
+            RA.n1 = S.n1;
+            RA.open = S.ld;
+            RA.err = S.err;
+            RA.diag = S.diag;
+            const RoundCount rc = tile_round(RA);
+            slide += rc.slide;
+            mism += rc.mism;
             __syncthreads();
-            const int n1 = min(*S.n1, LB);
+            if (*S.err != 0) {
+                outcome = 3;
+                break;
+            }
+            const int n1 = *S.n1;
             if (n1 > 0) {
-                // one warp per open slide; still-open ones get the whole CTA
+                // one warp per open slide; those still open get the whole CTA
                 for (int j = warp; j < n1; j += nw) {
-                    const int64_t d = S.ld[j], pos = S.lpos[j], lim = S.llim[j];
+                    const int64_t d = S.ld[j];
+                    const int64_t c = start_row(prev, off, d, t, n, m);
+                    const int64_t lim = c + min(n - c, m - c - d);
                     bool open;
-                    const int64_t l = slide_warp(Pr.A, n, Pr.B, m, pos, pos + d, 0, lim - pos,
-                                                 Bg.t2_cap, &open);
+                    const int64_t l = warp_slide(A, n, B, m, c, d, lim - c, Bg.t2_cap, &open);
                     if (lane == 0) {
                         if (!open) {
-                            S.llim[j] = -(pos + l) - 1; // negative: final row, encoded
-                        } else {
-                            S.lpos[j] = pos + l;
+                            cur[d - off] = (int32_t)(c + l);
+                            slide += l;
+                            mism += (c + l < lim);
+                            S.ld[j] = INT32_MIN; // finished
                         }
                     }
                 }
                 __syncthreads();
                 for (int j = 0; j < n1; j++) {
-                    const int64_t ll = S.llim[j];
-                    int64_t row;
-                    if (ll < 0) {
-                        row = -ll - 1;
-                    } else {
-                        row = cta_slide(Pr, S.ld[j], S.lpos[j], ll, S.smin);
-                    }
+                    const int64_t d = S.ld[j];
+                    if (d == INT32_MIN)
+                        continue;
+                    const int64_t c = start_row(prev, off, d, t, n, m);
+                    const int64_t lim = c + min(n - c, m - c - d);
+                    const int64_t row = cta_slide(A, n, B, m, d, c, lim, S.smin);
                     if (tid == 0) {
-                        const int64_t d = S.ld[j], c = S.lc[j];
-                        cur[d + H + 1] = (int32_t)row;
-                        const int64_t full_abs = c + min(n - c, m - c - d);
+                        cur[d - off] = (int32_t)row;
                         slide += row - c;
-                        mism += (row < full_abs);
+                        mism += (row < lim);
                     }
                 }
                 __syncthreads();
                 if (tid == 0)
                     *S.n1 = 0;
             }
-            const bool fin = ((target >= lo && target <= hi) && cur[target + H + 1] == n) ||
-                             *(volatile int32_t *)&Pr.state == 3;
+            const bool fin = (target >= lo && target <= hi) && cur[target - off] == n;
             __syncthreads();
             if (fin) {
                 outcome = 1;
@@ -231,14 +224,19 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
             mism += __shfl_down_sync(0xffffffffu, mism, o);
         }
         if (lane == 0) {
-            if (slide) atomicAdd(&Pr.slide, slide);
-            if (mism) atomicAdd(&Pr.mism, mism);
+            if (slide)
+                atomicAdd(&Pr.slide, slide);
+            if (mism)
+                atomicAdd(&Pr.mism, mism);
         }
-        __syncthreads();
-        const bool failed = *(volatile int32_t *)&Pr.state == 3;
-        __syncthreads();
-        if (failed) {
-            // leave the self-check record for the host
+        if (outcome == 3) {
+            // a start row outside the grid was recorded, never loaded
+            if (tid == 0) {
+                Pr.check[0] = (long long)S.diag[2];
+                Pr.check[1] = (long long)S.diag[3];
+                Pr.check[2] = (long long)S.diag[4];
+                Pr.state = 3;
+            }
         } else if (outcome == 1) {
             if (tid == 0) {
                 Pr.k = t;
@@ -246,12 +244,19 @@ __global__ void __launch_bounds__(BT) lv_batch_kernel(BatchArgs Bg, uint64_t bud
                 Pr.state = 1;
             }
         } else {
-            // save the last completed round (t - 1) as the resident frontier
+            // save the last completed round (t - 1) as the resident frontier;
+            // its furthest row tells the host how far along the pair is
             const int32_t *src = S.f[(t - 1) & 1];
-            for (int i = tid; i < Bg.W + 3; i += nt)
+            int r = 0;
+            for (int i = tid; i < Bg.W + 3; i += nt) {
                 Pr.front[i] = src[i];
+                r = max(r, src[i]);
+            }
+            atomicMax(S.reach, r);
+            __syncthreads();
             if (tid == 0) {
                 Pr.t = (int32_t)(t - 1);
+                Pr.reach = *S.reach;
                 Pr.state = outcome == 2 ? 2 : 0;
             }
         }
@@ -271,5 +276,17 @@ cudaError_t launch_lv_batch(const BatchArgs &B, int grid, cudaStream_t s, uint64
 }
 
 int lv_batch_threads() { return BT; }
+
+int lv_batch_ctas_per_sm(int W)
+{
+    const size_t smem = lv_batch_smem_bytes(W);
+    if (cudaFuncSetAttribute(lv_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return 1;
+    int nb = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, lv_batch_kernel, BT, smem) != cudaSuccess)
+        return 1;
+    return nb > 0 ? nb : 1;
+}
 
 } // namespace edg

@@ -8,7 +8,8 @@ namespace edg {
 
 // status codes written by kernels
 constexpr uint32_t ST_TIMEOUT = 4;
-constexpr uint32_t ST_LIMIT = 7;
+constexpr uint32_t ST_LIMIT = 7;  // the round cap was reached
+constexpr uint32_t ST_WIDE = 8;   // per pair: the band outgrew its group's tiles
 
 constexpr int CTA_THREADS = 512;   // threads of a tile CTA
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
@@ -17,6 +18,9 @@ constexpr int CHUNK_UNROLL = 8;
 constexpr int CHUNK_BYTES = CTA_THREADS * 16 * CHUNK_UNROLL; // 64 KiB per claim
 constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
 constexpr uint32_t CLAIM_CLOSED = 0xffffffffu;
+constexpr int MAX_CLS = 12;        // group-size classes of one tile launch
+// done_k of a pair that ended without a distance (status in its R_STATUS)
+constexpr unsigned long long DONE_STOPPED = ~0ull - 1;
 
 // A long slide open for help.  Each CTA owns one slot.  `claim` packs the
 // job id (high 32 bits) and the next unclaimed 64 KiB chunk (low 32 bits,
@@ -46,6 +50,7 @@ struct PairDesc {
 // Per group of CTAs (zeroed before the launch).
 struct __align__(64) GroupCtl {
     unsigned long long done_k; // ~0 until the tile owning d = m - n finds k
+                               // (DONE_STOPPED: the pair ended without it)
     uint32_t bar_count, bar_gen;
     uint32_t epoch_req;        // epoch changes requested (for CTAs without a tile)
     uint32_t epoch_t;          // round at which the last epoch change happens
@@ -57,8 +62,8 @@ struct __align__(64) GroupCtl {
 // Per launch (zeroed before the launch).
 struct __align__(64) LaunchCtl {
     uint32_t error;
-    uint32_t queue;            // next pair of the queue
-    uint32_t pad[14];
+    uint32_t queue[MAX_CLS];   // next pair of each class's queue
+    uint32_t pad[3];
     // where the first failed wait gave up: site, CTA, round, awaited value,
     // values seen, done_k
     unsigned long long diag[8];
@@ -83,17 +88,25 @@ enum {
     R_COUNT = 14
 };
 
+// The CTAs of a tile launch are cut into groups by class: class c has
+// groups of cls_G[c] CTAs on CTAs [cls_c0[c], cls_c0[c+1]), numbered from
+// cls_g0[c], and runs pairs [cls_p0[c], cls_p0[c+1]) of the pair list first,
+// then those of the classes below it (smaller groups, narrower bands).  A
+// group's re-tiling buffers (2 of 2*kc+5 entries, kc = cls_kc[c]) start at
+// gf + cls_gf[c] + (its index in the class) * 2 * (2*kc+5).
 struct LvArgs {
     const PairDesc *pairs;
     int32_t npairs;
-    int32_t group_size;   // CTAs per group; groups = gridDim.x / group_size
+    int32_t ncls;
+    int32_t cls_G[MAX_CLS], cls_c0[MAX_CLS + 1], cls_g0[MAX_CLS], cls_p0[MAX_CLS + 1];
+    int32_t cls_kc[MAX_CLS];
+    int64_t cls_gf[MAX_CLS];
     GroupCtl *gctl;
     LaunchCtl *ctl;
     JobSlot *slots;       // gridDim.x slots
     int32_t *halo;        // [gridDim.x][2 parity][2 sides][HMAX]
-    int32_t *gf;          // per group: 2 buffers of 2*kcap+5 entries
-    int64_t gf_stride;    // entries per group (2 buffers)
-    int32_t kcap;         // largest epoch radius the buffers hold
+    int32_t *gf;
+    int32_t kcap;         // round cap (largest epoch radius)
     int32_t smax;         // tile width capacity (shared memory)
     int32_t h;            // rounds per temporal block (1..HMAX)
     int32_t s0;           // initial tile width
@@ -118,6 +131,7 @@ struct BatchPair {
     int32_t t;         // rounds completed so far (-1 = not started)
     int32_t state;     // 0 running, 1 done, 2 needs the tile kernel, 3 self-check failed
     int64_t k;
+    int64_t reach;     // when parked: the furthest row of the saved frontier
     unsigned long long slide, mism;
     long long check[3]; // self-check record: round, diagonal, start row
 };
@@ -139,6 +153,7 @@ size_t lv_batch_smem_bytes(int W);
 // claiming (0 = run every pair to the end)
 cudaError_t launch_lv_batch(const BatchArgs &B, int grid, cudaStream_t s, uint64_t budget_ns);
 int lv_batch_threads();
+int lv_batch_ctas_per_sm(int W); // resident CTAs per SM (registers, shared memory)
 
 // ---------------------------------------------------------------- tests
 struct HashArgs {

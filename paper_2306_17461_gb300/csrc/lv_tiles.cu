@@ -33,6 +33,7 @@
 //    place it gave up) instead of hanging.
 #include "ed_device.cuh"
 #include "lv_kernels.cuh"
+#include "lv_round.cuh"
 
 namespace edg {
 
@@ -135,102 +136,6 @@ __device__ __forceinline__ int64_t finish_slide(const Pair &Q, int64_t c, int64_
         C.mism += (p < full_abs);
     }
     return p;
-}
-
-// ------------------------------------------------------------------ phase A
-constexpr int DPT = 4; // diagonals per thread per batch
-
-struct RoundArgs {
-    const uint8_t *A, *B;
-    int64_t n, m;
-    const int32_t *prev;     // round tau-1, indexed d - off
-    int32_t *cur;            // round tau
-    int64_t off, lo, hi, tau, a, b;
-    int t1_cap;
-    int *n1;
-    int32_t *open;           // diagonals whose slide is still open
-    uint32_t *err;           // launch status word (self-check records)
-    unsigned long long *diag;
-};
-struct RoundCount {
-    unsigned long long slide, mism;
-};
-
-// The start row of diagonal d in round tau from the three predecessors,
-// clamped to the diagonal's last cell.
-__device__ __forceinline__ int64_t start_row(const int32_t *prev, int64_t off, int64_t d, int64_t tau,
-                                             int64_t n, int64_t m)
-{
-    if (tau == 0)
-        return 0;
-    const int64_t x1 = prev[d - 1 - off];
-    const int64_t x2 = (int64_t)prev[d - off] + 1;
-    const int64_t x3 = (int64_t)prev[d + 1 - off] + 1;
-    return min(max(x1, max(x2, x3)), min(n, m - d));
-}
-
-// One round over diagonals [lo, hi] of the tile (strided over the CTA): the
-// start row, then the per-thread slide.  DPT diagonals per thread are
-// handled together so that their first loads are in flight together.
-// Diagonals whose slide is still open after t1_cap bytes are listed; the
-// list holds one entry per computed diagonal at most, so it cannot fill.
-// Counts only diagonals of [a, b).
-__device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
-{
-    RoundCount out = {0, 0};
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t base = R.lo; base <= R.hi; base += (int64_t)nt * DPT) {
-        int64_t c[DPT];
-        uint32_t wa[DPT], wb[DPT];
-#pragma unroll
-        for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            c[u] = 0;
-            wa[u] = wb[u] = 0;
-            if (d <= R.hi) {
-                c[u] = start_row(R.prev, R.off, d, R.tau, R.n, R.m);
-                if (c[u] < 0 || c[u] + d < 0) {
-                    // a start row outside the grid: record it, never load it
-                    if (atomicCAS(R.err, 0u, 6u) == 0u) {
-                        R.diag[0] = 6;
-                        R.diag[1] = blockIdx.x;
-                        R.diag[2] = (unsigned long long)R.tau;
-                        R.diag[3] = (unsigned long long)d;
-                        R.diag[4] = (unsigned long long)c[u];
-                        R.diag[5] = ((unsigned long long)(uint32_t)R.prev[d - 1 - R.off] << 32) |
-                                    (uint32_t)R.prev[d + 1 - R.off];
-                        R.diag[6] = (unsigned long long)R.off;
-                    }
-                    c[u] = 0;
-                } else if (min(R.n - c[u], R.m - c[u] - d) > 0) {
-                    word_load(R.A, R.B, c[u], c[u] + d, wa[u], wb[u]);
-                }
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            if (d <= R.hi) {
-                const int64_t cc = c[u];
-                const int64_t full = min(R.n - cc, R.m - cc - d);
-                bool op = false;
-                int64_t av = 0;
-                int64_t l = word_slide(R.A, R.B, cc, cc + d, full, wa[u], wb[u], &av);
-                if (l < 0) // rare: the words matched; 16-byte windows, out of line
-                    l = slide_more(R.A, R.n, R.B, R.m, cc, cc + d, av, full, R.t1_cap, &op);
-                if (!op) {
-                    R.cur[d - R.off] = (int32_t)(cc + l);
-                    if (d >= R.a && d < R.b) {
-                        out.slide += l;
-                        out.mism += (l < full);
-                    }
-                } else {
-                    R.open[atomicAdd(R.n1, 1)] = (int32_t)d;
-                }
-            }
-        }
-    }
-    return out;
 }
 
 // ------------------------------------------------------------------ jobs
@@ -642,9 +547,35 @@ __device__ __noinline__ void open_slides(const LvArgs &P, const Smem &S, const P
     __syncthreads();
 }
 
-// Runs one pair on the group.  Returns false if the launch must stop.
+// The largest epoch radius whose band [max(-R, -n), min(R, m)] fits in
+// cap diagonals; the band width min(R, m) + min(R, n) + 1 grows with R.
+__device__ int64_t fit_radius(int64_t n, int64_t m, int64_t cap)
+{
+    int64_t lo = 0, hi = max(n, m);
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo + 1) / 2;
+        if (min(mid, m) + min(mid, n) + 1 <= cap)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Ends the pair for the whole group without a distance: its band outgrew
+// the group's tiles (ST_WIDE: the host runs it again on a larger group) or
+// the round cap was reached (ST_LIMIT).  The first CTA here records the
+// status; the others see done_k set at their next check or barrier.
+__device__ void pair_stop(const PairDesc &D, GroupCtl *gc, uint32_t status)
+{
+    if (threadIdx.x == 0 && atomicCAS(&gc->done_k, ~0ull, DONE_STOPPED) == ~0ull)
+        D.res[R_STATUS] = status;
+}
+
+// Runs one pair on the group; kc is the radius its re-tiling buffers hold.
+// Returns false if the launch must stop.
 __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, GroupCtl *gc, int gi, int G,
-                         int c0, int32_t *gfb, unsigned long long iter, Counters &C)
+                         int c0, int32_t *gfb, int64_t kc, unsigned long long iter, Counters &C)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int h = P.h;
@@ -657,7 +588,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     Q.TB = D.TB;
     Q.hash = P.use_hash && D.TA && D.TB;
     const int64_t n = Q.n, m = Q.m, target = m - n, nm = max(n, m);
-    const int64_t gstride = 2 * (int64_t)P.kcap + 5;
+    const int64_t gstride = 2 * kc + 5;
     const bool leader = (gi == 0 && tid == 0);
     // epoch 0
     int64_t R = min((int64_t)P.s0 * G / 2, (int64_t)P.kcap);
@@ -666,9 +597,8 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     uint32_t epoch = 0;
     Tile T = partition(Q, R, G, gi, c0, h);
     if (T.S > P.smax) {
-        if (tid == 0)
-            set_error(P, ST_LIMIT);
-        return false;
+        pair_stop(D, gc, ST_WIDE);
+        return true;
     }
     for (int i = tid; i < P.smax + 2 * HMAX + 2; i += nt) {
         S.F[0][i] = NEG;
@@ -735,17 +665,22 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         if ((t + h - 1 > R) && (R < nm)) {
             // ------------------------------------------ epoch change
             const uint64_t te0 = clock64();
-            const int64_t Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
+            int64_t Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
             if (t + h - 1 > Rn && Rn < nm) {
-                if (tid == 0)
-                    set_error(P, ST_LIMIT);
-                return false;
+                pair_stop(D, gc, ST_LIMIT);
+                return true;
+            }
+            // no further than the group's tiles hold
+            Rn = min(Rn, fit_radius(n, m, (int64_t)G * P.smax));
+            if (t + h - 1 > Rn && Rn < nm) {
+                pair_stop(D, gc, ST_WIDE);
+                return true;
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
             if (T.has) {
                 const int32_t *src = S.F[(t - 1) & 1];
                 for (int64_t d = T.a + tid; d < T.b; d += nt)
-                    st_cg(buf + d + P.kcap + 2, src[d - (T.a - h) + 1]);
+                    st_cg(buf + d + kc + 2, src[d - (T.a - h) + 1]);
             }
             if (leader) {
                 gc->epoch_t = (uint32_t)t;
@@ -762,15 +697,14 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             R = Rn;
             T = partition(Q, R, G, gi, c0, h);
             if (T.S > P.smax) {
-                if (tid == 0)
-                    set_error(P, ST_LIMIT);
-                return false;
+                pair_stop(D, gc, ST_WIDE);
+                return true;
             }
             if (T.has) {
                 const int64_t plo = max(-(t - 1), -n), phi = min(t - 1, m);
                 int32_t *dst = S.F[(t - 1) & 1];
                 for (int64_t d = T.a - h + tid; d < T.b + h; d += nt)
-                    dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? ld_cg(buf + d + P.kcap + 2) : NEG;
+                    dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? ld_cg(buf + d + kc + 2) : NEG;
             }
             __syncthreads();
             C.tm[3] += clock64() - te0;
@@ -928,15 +862,29 @@ __device__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
 __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
 {
     const Smem S = carve(P);
-    const int G = P.group_size;
-    const int grp = blockIdx.x / G, gi = blockIdx.x % G, c0 = grp * G;
-    GroupCtl *gc = &P.gctl[grp];
-    int32_t *gfb = P.gf + (int64_t)grp * P.gf_stride;
+    int cls = 0;
+    while (cls + 1 < P.ncls && (int)blockIdx.x >= P.cls_c0[cls + 1])
+        cls++;
+    const int G = P.cls_G[cls];
+    const int rel = (int)blockIdx.x - P.cls_c0[cls];
+    const int gi = rel % G, c0 = (int)blockIdx.x - gi;
+    GroupCtl *gc = &P.gctl[P.cls_g0[cls] + rel / G];
+    const int64_t kc = P.cls_kc[cls];
+    int32_t *gfb = P.gf + P.cls_gf[cls] + (int64_t)(rel / G) * 2 * (2 * kc + 5);
     Counters C;
     for (unsigned long long iter = 1;; iter++) {
         if (gi == 0 && threadIdx.x == 0) {
-            const uint32_t q = atomicAdd(&P.ctl->queue, 1u);
-            gc->pair = q < (uint32_t)P.npairs ? (int32_t)q : -1;
+            // the class's own queue first, then the classes below it
+            int32_t q = -1;
+            for (int c = cls; c >= 0 && q < 0; c--) {
+                const uint32_t cnt = (uint32_t)(P.cls_p0[c + 1] - P.cls_p0[c]);
+                if (*(volatile uint32_t *)&P.ctl->queue[c] >= cnt)
+                    continue;
+                const uint32_t i = atomicAdd(&P.ctl->queue[c], 1u);
+                if (i < cnt)
+                    q = P.cls_p0[c] + (int32_t)i;
+            }
+            gc->pair = q;
             gc->done_k = ~0ull;
             gc->epoch_req = 0;
             gc->epoch_t = 0;
@@ -949,7 +897,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         if (q < 0)
             break;
         const PairDesc D = P.pairs[q];
-        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, iter, C);
+        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, iter, C);
         flush_counters(D, C, gi == 0);
         if (!ok)
             break;

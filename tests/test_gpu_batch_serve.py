@@ -44,6 +44,37 @@ def test_batch_dev_matches_oracle(ctx, orc):
     assert st["extensions"] > 0
 
 
+def _tail_burst_pair(n=200_000, k=16_000, tail=40_000, extra=0):
+    """Edits only in the last `tail` characters: the frontier runs far ahead
+    in the first rounds, so an estimate of the distance from early progress
+    is far too low."""
+    rng = W.rng_for(81, extra)
+    sym = W.Symbols(4)
+    A = sym.draw(rng, n)
+    pos = np.sort(rng.choice(np.arange(n - tail, n), size=k, replace=False))
+    return W.Pair(A, W.plant(rng, A, pos, sym), k, "tail burst")
+
+
+def test_batch_band_outgrows_estimated_group(orc):
+    """A parked pair placed on a group too small for its band ends with the
+    per-pair 'too wide' status and runs again on a larger group (one more
+    tile launch); every distance still equals the oracle's."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    c = ed.Context(device=0, grid_ctas=4)
+    try:
+        pairs = [W.make_pair(90 + i, 40_000, 2500, sigma=4) for i in range(2)]
+        pairs.append(_tail_burst_pair())
+        want = orc.many("lv", [(p.A, p.B) for p in pairs])
+        assert want[2] > 8192  # wider than one CTA's tiles hold
+        got = ed.ed_distance_batch_dev(c.h, [dev(p.A) for p in pairs], [dev(p.B) for p in pairs])
+        assert np.array_equal(got, want)
+        # the batch launch, the tile launch, and the retry of the wide pair
+        assert c.stats()["kernel_launches"] == 3
+    finally:
+        c.close()
+
+
 def test_batch_host_matches_oracle(ctx, orc):
     from paper_2306_17461_gb300 import binding as ed
 

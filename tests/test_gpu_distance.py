@@ -148,3 +148,17 @@ def test_large_workload_reduced(ctxs, orc):
     p = W.single_large(n=20_000_000, k=2000)
     want = orc.lv(p.A, p.B, nthreads=8)
     assert ctxs["default"].distance_dev(dev(p.A), dev(p.B)) == want
+
+
+def test_round_cap_is_reported():
+    """A pair needing more rounds than max_rounds ends with ED_ELIMIT, and
+    the context stays usable for the next pair."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    p = W.make_pair(95, 20_000, 300, sigma=4)
+    with ed.Context(device=0, max_rounds=64) as c:
+        with pytest.raises(ed.EdError) as e:
+            ed.ed_distance_dev(c.h, dev(p.A), dev(p.B))
+        assert e.value.code == ed.ED_ELIMIT
+        q = W.make_pair(96, 20_000, 20, sigma=4)
+        assert ed.ed_distance_dev(c.h, dev(q.A), dev(q.B)) <= 20
