@@ -436,6 +436,7 @@ def run_serve(args, D: Dist):
         "p50_ms": best["p50_ms"],
         "p99_ms": best["p99_ms"],
         "engine_steps": cnt["steps"],
+        "tile_slices": cnt["slices"],
     }
     return res, None
 
@@ -522,8 +523,8 @@ def main():
     ap.add_argument("--ks", default="10,1000,100000")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--npairs", type=int, default=4096)
-    ap.add_argument("--npairs-serve", type=int, default=512)
-    ap.add_argument("--rates", default="2,5,10,20")
+    ap.add_argument("--npairs-serve", type=int, default=128)
+    ap.add_argument("--rates", default="1,2,4")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

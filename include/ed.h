@@ -145,9 +145,12 @@ int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
               size_t m, uint64_t *ticket);
 int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k);
 
-/* Serving counters: admitted, completed, in flight, engine steps. */
+/* Serving counters: admitted, completed, in flight, engine steps, and
+ * slices (times a pair on the tile kernel was left at a sync point with its
+ * band frontier saved, to be resumed at the next step).  Null pointers are
+ * skipped. */
 int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed,
-                      uint64_t *inflight, uint64_t *steps);
+                      uint64_t *inflight, uint64_t *steps, uint64_t *slices);
 
 /* ---- building blocks, exported for tests and diagnostics ---------------- */
 

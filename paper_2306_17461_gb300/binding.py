@@ -79,7 +79,7 @@ _SIGS = {
     "ed_distance_batch": (_I, [_P, _S, _P, _P, _P, _P, _P]),
     "ed_submit": (_I, [_P, _P, _S, _P, _S, _P]),
     "ed_poll": (_I, [_P, _U64, _P]),
-    "ed_serve_counters": (_I, [_P, _P, _P, _P, _P]),
+    "ed_serve_counters": (_I, [_P, _P, _P, _P, _P, _P]),
     "ed_lcp_dev": (_I, [_P, _P, _S, _P, _S, _P, _P, _S, _I, _P, _P, _P, _P]),
     "ed_prefix_hash_dev": (_I, [_P, _P, _S, _P, _P]),
     "ed_hash_base": (_U64, [_P]),
@@ -261,9 +261,9 @@ def ed_poll(ctx, ticket: int):
 
 
 def ed_serve_counters(ctx) -> dict:
-    v = [ctypes.c_uint64() for _ in range(4)]
+    v = [ctypes.c_uint64() for _ in range(5)]
     _check(ctx, load().ed_serve_counters(ctx, *[ctypes.byref(x) for x in v]), "ed_serve_counters")
-    return dict(zip(["admitted", "completed", "inflight", "steps"], [int(x.value) for x in v]))
+    return dict(zip(["admitted", "completed", "inflight", "steps", "slices"], [int(x.value) for x in v]))
 
 
 def ed_lcp_dev(ctx, A, B, x, y, method: int, TA=None, TB=None, stream=None) -> np.ndarray:

@@ -110,6 +110,14 @@ struct Request {
     size_t bytesA = 0, bytesB = 0, bytesF = 0;
     int64_t n = 0, m = 0;
     int32_t t = -1;
+    // on the tile kernel (band wider than one batch CTA): its group size,
+    // resident frontier (keep, radius keep_r) and the round / radius to
+    // resume from (t0 = 0: from the start)
+    int tile_G = 0;
+    double cost = 0.0;
+    char *keep = nullptr;
+    size_t bytesK = 0;
+    int64_t keep_r = 0, t0 = 0, R0 = 0;
 };
 
 // One pair handed to the tile kernel.
@@ -121,6 +129,17 @@ struct TileJob {
     int64_t dump_tmax;
     int G;       // CTAs of the group the pair runs on (1 .. grid)
     double cost; // estimated run time (any unit), to share CTAs among classes
+    // resident frontier for time slicing (serving), or null
+    int32_t *keep = nullptr;
+    int64_t keep_r = 0, t0 = 0, R0 = 0;
+};
+
+// What a tile launch left for one pair: its distance (st 0), or ST_WIDE,
+// ST_LIMIT, or ST_SUSPENDED with the round and radius to resume from.
+struct TileOut {
+    uint64_t k = 0;
+    uint32_t st = 0;
+    int64_t rt = 0, rr = 0;
 };
 
 } // namespace
@@ -150,7 +169,7 @@ struct ed_ctx {
     std::mutex smu;
     std::condition_variable scv;
     bool stop = false;
-    bool engine_on = false;
+    std::atomic<bool> engine_on{false};
     Arena arena;
     DevBuf arena_buf;
     std::deque<Request *> pending;
@@ -158,7 +177,7 @@ struct ed_ctx {
     std::map<uint64_t, int64_t> results; // ticket -> k (or negative status)
     std::map<uint64_t, bool> known;
     uint64_t next_ticket = 1;
-    uint64_t n_admitted = 0, n_completed = 0, n_steps = 0;
+    uint64_t n_admitted = 0, n_completed = 0, n_steps = 0, n_slices = 0;
     cudaStream_t sstream = nullptr, cstream = nullptr;
     DevBuf s_pairs, s_order, s_next;
 };
@@ -261,11 +280,11 @@ int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB
 // One tile launch over the jobs, CTA groups by class (one class per group
 // size wanted).  Every class that fits gets one group, largest first; the
 // remaining CTAs go, one group at a time, to the class whose estimated run
-// time per group is highest.  k[i] and st[i] receive each pair's distance
-// and status (0, ST_WIDE, ST_LIMIT); the counters of finished pairs are
-// summed into ctx->last.
-static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s,
-                          std::vector<uint64_t> &k, std::vector<uint32_t> &st)
+// time per group is highest.  out[i] receives each pair's outcome; the
+// counters of pairs that finished or were suspended are summed into
+// ctx->last.  budget_ns > 0 time-slices the pairs that have a keep buffer.
+static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s, uint64_t budget_ns,
+                          std::vector<TileOut> &out)
 {
     int r;
     const int np = (int)jobs.size();
@@ -391,6 +410,10 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
         pd[q].res = (unsigned long long *)ctx->res.p + (size_t)R_COUNT * q;
         pd[q].dump = j.dump;
         pd[q].dump_tmax = (int32_t)j.dump_tmax;
+        pd[q].keep = j.keep;
+        pd[q].keep_r = j.keep_r;
+        pd[q].t0 = j.t0;
+        pd[q].R0 = j.R0;
     }
     P.pairs = (const PairDesc *)ctx->pdesc.p;
     P.npairs = np;
@@ -409,6 +432,8 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
     P.spin_ns = ctx->cfg.spin_limit_ns;
     P.idle_ns = ctx->cfg.spin_limit_ns * 60;
+    P.budget_ns = budget_ns;
+    P.sync_rounds = 16 * h;
     CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->ctl.p, 0, sizeof(LaunchCtl), s));
     CK(cudaMemsetAsync(ctx->gctl.p, 0, sizeof(GroupCtl) * ngroups, s));
@@ -436,16 +461,25 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
         ctx->last_err = buf;
         return lst;
     }
-    k.assign(np, 0);
-    st.assign(np, 0);
+    out.assign(np, TileOut{});
     for (int q = 0; q < np; q++) {
         const int i = ord[q];
         const unsigned long long *R = ctx->h_res + (size_t)R_COUNT * q;
-        st[i] = (uint32_t)R[R_STATUS];
-        if (st[i] != 0)
+        TileOut &o = out[i];
+        o.st = (uint32_t)R[R_STATUS];
+        if (o.st == ST_SUSPENDED) {
+            o.rt = (int64_t)R[R_RESUME_T];
+            o.rr = (int64_t)R[R_RESUME_R];
+            // rounds t0 .. rt - 1 done in this launch
+            ctx->last.extensions += count_extensions(jobs[i].n, jobs[i].m, o.rt - 1) -
+                                    (jobs[i].t0 > 0 ? count_extensions(jobs[i].n, jobs[i].m, jobs[i].t0 - 1) : 0);
+        } else if (o.st != 0) {
             continue;
-        k[i] = R[R_K];
-        ctx->last.extensions += count_extensions(jobs[i].n, jobs[i].m, (int64_t)R[R_K]);
+        } else {
+            o.k = R[R_K];
+            ctx->last.extensions += count_extensions(jobs[i].n, jobs[i].m, (int64_t)R[R_K]) -
+                                    (jobs[i].t0 > 0 ? count_extensions(jobs[i].n, jobs[i].m, jobs[i].t0 - 1) : 0);
+        }
         ctx->last.slide_chars += R[R_SLIDE];
         ctx->last.compared_bytes += 2ull * (R[R_SLIDE] + R[R_MISMATCH]);
         ctx->last.long_slides += R[R_LONG];
@@ -474,17 +508,16 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s, std
     for (size_t i = 0; i < idx.size(); i++)
         idx[i] = i;
     while (!cur.empty()) {
-        std::vector<uint64_t> kk;
-        std::vector<uint32_t> st;
-        int r = run_tiles_once(ctx, cur, s, kk, st);
+        std::vector<TileOut> o;
+        int r = run_tiles_once(ctx, cur, s, 0, o);
         if (r != ED_OK)
             return r;
         std::vector<TileJob> next;
         std::vector<size_t> nidx;
         for (size_t i = 0; i < cur.size(); i++) {
-            if (st[i] == 0) {
-                k[idx[i]] = kk[i];
-            } else if (st[i] == ST_WIDE && cur[i].G < ctx->grid) {
+            if (o[i].st == 0) {
+                k[idx[i]] = o[i].k;
+            } else if (o[i].st == ST_WIDE && cur[i].G < ctx->grid) {
                 TileJob j = cur[i];
                 j.G = std::min(ctx->grid, 2 * std::max(1, j.G));
                 next.push_back(j);
@@ -492,8 +525,8 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s, std
             } else {
                 char buf[160];
                 std::snprintf(buf, sizeof(buf), "pair %zu: %s", idx[i],
-                              st[i] == ST_WIDE ? "band wider than the whole grid's tiles hold"
-                                               : "more rounds than the configured cap");
+                              o[i].st == ST_WIDE ? "band wider than the whole grid's tiles hold"
+                                                 : "more rounds than the configured cap");
                 ctx->last_err = buf;
                 return ED_ELIMIT;
             }
@@ -991,9 +1024,38 @@ int ed_distance_batch(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
 }
 
 // ------------------------------------------------------------------ serving
-// One engine step: every live pair gets up to ~2 ms of device time in one
-// launch of the batch kernel (frontiers stay resident in the arena); pairs
-// whose band outgrew one CTA are finished together on tile-kernel groups.
+// Device time per engine step: the batch kernel (pairs within one CTA's
+// band), then the tile kernel (pairs whose band outgrew it).
+constexpr uint64_t SERVE_BATCH_NS = 2000000;
+constexpr uint64_t SERVE_TILE_NS = 4000000;
+
+static void release_request(ed_ctx *ctx, Request *q)
+{
+    ctx->arena.release(q->dA, q->bytesA);
+    ctx->arena.release(q->dB, q->bytesB);
+    ctx->arena.release(q->front, q->bytesF);
+    ctx->arena.release(q->keep, q->bytesK);
+}
+
+// Moves a request to the tile kernel on a group of G CTAs, with a resident
+// frontier as wide as that group's tiles (none if the arena is full: the
+// pair then runs to its end in one launch).
+static void to_tiles(ed_ctx *ctx, Request *q, int G)
+{
+    ctx->arena.release(q->keep, q->bytesK);
+    q->tile_G = G;
+    q->keep_r = std::min<int64_t>(std::max(q->n, q->m), (int64_t)G * SMAX_LIMIT);
+    q->bytesK = sizeof(int32_t) * (size_t)(2 * q->keep_r + 5);
+    q->keep = ctx->arena.alloc(q->bytesK);
+    q->t0 = 0;
+    q->R0 = 0;
+}
+
+// One engine step: the live pairs not yet on the tile kernel get up to
+// SERVE_BATCH_NS in one launch of the batch kernel (frontiers resident in
+// the arena); those whose band outgrew a CTA move to the tile kernel, where
+// every such pair gets up to SERVE_TILE_NS per step and its band frontier
+// stays resident between steps.
 static void engine_loop(ed_ctx *ctx)
 {
     cudaSetDevice(ctx->device);
@@ -1013,11 +1075,18 @@ static void engine_loop(ed_ctx *ctx)
         }
         std::unique_lock<std::mutex> api(ctx->api_mu);
         const size_t L = ctx->live.size();
-        hp.resize(L);
-        order.resize(L);
-        for (size_t i = 0; i < L; i++) {
-            Request *q = ctx->live[i];
-            BatchPair &b = hp[i];
+        std::vector<int64_t> result(L, 0);
+        std::vector<char> done(L, 0);
+        // (1) the batch kernel
+        std::vector<size_t> bidx;
+        for (size_t i = 0; i < L; i++)
+            if (!ctx->live[i]->tile_G)
+                bidx.push_back(i);
+        hp.resize(bidx.size());
+        order.resize(bidx.size());
+        for (size_t j = 0; j < bidx.size(); j++) {
+            Request *q = ctx->live[bidx[j]];
+            BatchPair &b = hp[j];
             b = BatchPair{};
             b.A = (const uint8_t *)q->dA;
             b.B = (const uint8_t *)q->dB;
@@ -1026,55 +1095,89 @@ static void engine_loop(ed_ctx *ctx)
             b.front = (int32_t *)q->front;
             b.t = q->t;
             b.k = -1;
-            order[i] = (int32_t)i;
+            order[j] = (int32_t)j;
         }
-        const uint64_t grid = (uint64_t)ctx->num_sms * lv_batch_ctas_per_sm(BATCH_W);
-        std::rotate(order.begin(), order.begin() + (ctx->n_steps * grid) % L, order.end());
-        const int rc = batch_launch(ctx, hp, order, ctx->s_pairs, ctx->s_order, ctx->s_next, ctx->sstream,
-                                    2000000ull);
-        ctx->n_steps++;
-        // pairs parked by the batch kernel: finish them on the tile kernel
-        std::vector<size_t> parked;
-        std::vector<TileJob> jobs;
-        if (rc == ED_OK) {
+        if (!bidx.empty()) {
+            const uint64_t grid = (uint64_t)ctx->num_sms * lv_batch_ctas_per_sm(BATCH_W);
+            std::rotate(order.begin(), order.begin() + (ctx->n_steps * grid) % bidx.size(), order.end());
+            const int rc = batch_launch(ctx, hp, order, ctx->s_pairs, ctx->s_order, ctx->s_next, ctx->sstream,
+                                        SERVE_BATCH_NS);
+            int64_t tile_sum = 0;
             for (size_t i = 0; i < L; i++)
-                if (hp[i].state == 2) {
-                    parked.push_back(i);
-                    jobs.push_back(parked_job(ctx, hp[i]));
+                tile_sum += ctx->live[i]->tile_G;
+            for (size_t j = 0; j < bidx.size(); j++) {
+                Request *q = ctx->live[bidx[j]];
+                const BatchPair &b = hp[j];
+                if (rc != ED_OK) {
+                    result[bidx[j]] = rc;
+                    done[bidx[j]] = 1;
+                } else if (b.state == 1) {
+                    result[bidx[j]] = b.k;
+                    done[bidx[j]] = 1;
+                } else if (b.state == 2) {
+                    // group from the distance estimate, doubled while the
+                    // tile pairs would fill at most half of the grid
+                    const TileJob pj = parked_job(ctx, b);
+                    int G = pj.G;
+                    while (G < ctx->grid && 2 * (tile_sum + 2 * G) <= ctx->grid)
+                        G *= 2;
+                    G = std::min(G, ctx->grid);
+                    tile_sum += G;
+                    q->cost = pj.cost;
+                    to_tiles(ctx, q, G);
+                } else {
+                    q->t = b.t;
                 }
+            }
         }
-        std::vector<uint64_t> kk;
-        int rt = ED_OK;
+        ctx->n_steps++;
+        // (2) the tile kernel, time-sliced
+        std::vector<size_t> tidx;
+        std::vector<TileJob> jobs;
+        for (size_t i = 0; i < L; i++) {
+            Request *q = ctx->live[i];
+            if (!q->tile_G || done[i])
+                continue;
+            TileJob j{(const uint8_t *)q->dA, (const uint8_t *)q->dB, q->n, q->m, nullptr, nullptr, nullptr, 0,
+                      q->tile_G, q->cost};
+            j.keep = (int32_t *)q->keep;
+            j.keep_r = q->keep ? q->keep_r : 0;
+            j.t0 = q->keep ? q->t0 : 0;
+            j.R0 = q->R0;
+            tidx.push_back(i);
+            jobs.push_back(j);
+        }
         if (!jobs.empty()) {
-            spread_jobs(ctx, jobs);
-            rt = run_tiles(ctx, jobs, ctx->sstream, kk);
+            std::vector<TileOut> o;
+            const int rt = run_tiles_once(ctx, jobs, ctx->sstream, SERVE_TILE_NS, o);
+            for (size_t j = 0; j < tidx.size(); j++) {
+                Request *q = ctx->live[tidx[j]];
+                if (rt != ED_OK) {
+                    result[tidx[j]] = rt;
+                    done[tidx[j]] = 1;
+                } else if (o[j].st == 0) {
+                    result[tidx[j]] = (int64_t)o[j].k;
+                    done[tidx[j]] = 1;
+                } else if (o[j].st == ST_SUSPENDED) {
+                    q->t0 = o[j].rt;
+                    q->R0 = o[j].rr;
+                    ctx->n_slices++;
+                } else if (o[j].st == ST_WIDE && q->tile_G < ctx->grid) {
+                    to_tiles(ctx, q, std::min(ctx->grid, 2 * q->tile_G)); // again, from round 0
+                } else {
+                    result[tidx[j]] = ED_ELIMIT;
+                    done[tidx[j]] = 1;
+                }
+            }
         }
         api.unlock();
         std::vector<Request *> still;
         for (size_t i = 0; i < L; i++) {
             Request *q = ctx->live[i];
-            const BatchPair &b = hp[i];
-            int64_t result = 0;
-            bool done = false;
-            if (rc != ED_OK) {
-                result = rc;
-                done = true;
-            } else if (b.state == 1) {
-                result = b.k;
-                done = true;
-            } else if (b.state == 2) {
-                const size_t j = (size_t)(std::find(parked.begin(), parked.end(), i) - parked.begin());
-                result = rt == ED_OK ? (int64_t)kk[j] : rt;
-                done = true;
-            } else {
-                q->t = b.t;
-            }
-            if (done) {
-                ctx->arena.release(q->dA, q->bytesA);
-                ctx->arena.release(q->dB, q->bytesB);
-                ctx->arena.release(q->front, q->bytesF);
+            if (done[i]) {
+                release_request(ctx, q);
                 std::lock_guard<std::mutex> lk(ctx->smu);
-                ctx->results[q->ticket] = result;
+                ctx->results[q->ticket] = result[i];
                 ctx->n_completed++;
                 delete q;
             } else {
@@ -1088,6 +1191,10 @@ static void engine_loop(ed_ctx *ctx)
 
 static int engine_start(ed_ctx *ctx)
 {
+    // checked before the lock too: the engine holds api_mu through each
+    // step, and submitters must not queue behind it once it runs
+    if (ctx->engine_on.load(std::memory_order_acquire))
+        return ED_OK;
     std::lock_guard<std::mutex> g(ctx->api_mu);
     if (ctx->engine_on)
         return ED_OK;
@@ -1204,7 +1311,7 @@ int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k)
 }
 
 int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed, uint64_t *inflight,
-                      uint64_t *steps)
+                      uint64_t *steps, uint64_t *slices)
 {
     if (!ctx)
         return ED_EINVAL;
@@ -1217,6 +1324,8 @@ int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed, uint
         *inflight = ctx->live.size() + ctx->pending.size();
     if (steps)
         *steps = ctx->n_steps;
+    if (slices)
+        *slices = ctx->n_slices;
     return ED_OK;
 }
 

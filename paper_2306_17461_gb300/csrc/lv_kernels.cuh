@@ -10,6 +10,7 @@ namespace edg {
 constexpr uint32_t ST_TIMEOUT = 4;
 constexpr uint32_t ST_LIMIT = 7;  // the round cap was reached
 constexpr uint32_t ST_WIDE = 8;   // per pair: the band outgrew its group's tiles
+constexpr uint32_t ST_SUSPENDED = 9; // per pair: budget spent, frontier saved to keep
 
 constexpr int CTA_THREADS = 512;   // threads of a tile CTA
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
@@ -45,6 +46,11 @@ struct PairDesc {
     int32_t *dump;             // frontier dump (tests) or null
     int32_t dump_tmax;
     int32_t pad;
+    // resident frontier across launches (serving) or null: L_{t-1}[d] at
+    // keep[d + keep_r + 2] for |d| <= keep_r; the pair starts at round t0
+    // with epoch radius R0 when t0 > 0
+    int32_t *keep;
+    int64_t keep_r, t0, R0;
 };
 
 // Per group of CTAs (zeroed before the launch).
@@ -56,7 +62,8 @@ struct __align__(64) GroupCtl {
     uint32_t epoch_t;          // round at which the last epoch change happens
     int32_t pair;              // pair index being run (-1: none left)
     uint32_t ebar_count, ebar_gen; // epoch-change barrier (abandoned once k is known)
-    uint32_t pad[7];
+    uint32_t susp[2];          // epoch e ends the launch's share of the pair: susp[e & 1]
+    uint32_t pad[5];
 };
 
 // Per launch (zeroed before the launch).
@@ -85,7 +92,9 @@ enum {
     // device time (ns, seen by thread 0 of the group's first CTA): rounds,
     // open slides, halo waits (helping included), epoch changes, spare
     R_T0 = 8,
-    R_COUNT = 14
+    R_RESUME_T = 14,  // suspended: the round to start from, and the radius
+    R_RESUME_R = 15,
+    R_COUNT = 16
 };
 
 // The CTAs of a tile launch are cut into groups by class: class c has
@@ -116,6 +125,11 @@ struct LvArgs {
     uint64_t pow2[62];    // p^(2^j) mod 2^61-1 (hash LCP)
     uint64_t spin_ns;     // bound of one wait on a peer's progress
     uint64_t idle_ns;     // bound of a wait that may span other CTAs' work
+    // time slicing: with budget_ns > 0, a group on a pair with a keep
+    // buffer meets every sync_rounds rounds and saves and leaves the pair
+    // once budget_ns have passed since the launch started
+    uint64_t budget_ns;
+    int32_t sync_rounds;
 };
 
 size_t lv_tiles_smem_bytes(int smax, int h);

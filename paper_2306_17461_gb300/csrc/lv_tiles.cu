@@ -575,7 +575,8 @@ __device__ void pair_stop(const PairDesc &D, GroupCtl *gc, uint32_t status)
 // Runs one pair on the group; kc is the radius its re-tiling buffers hold.
 // Returns false if the launch must stop.
 __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, GroupCtl *gc, int gi, int G,
-                         int c0, int32_t *gfb, int64_t kc, unsigned long long iter, Counters &C)
+                         int c0, int32_t *gfb, int64_t kc, unsigned long long iter, uint64_t deadline,
+                         Counters &C)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int h = P.h;
@@ -590,13 +591,20 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     const int64_t n = Q.n, m = Q.m, target = m - n, nm = max(n, m);
     const int64_t gstride = 2 * kc + 5;
     const bool leader = (gi == 0 && tid == 0);
-    // epoch 0
+    // a pair with a keep buffer may be left at a sync point and resumed
+    const bool can_suspend = P.budget_ns != 0 && D.keep != nullptr;
+    // epoch 0, or the saved round and radius of a resumed pair
     int64_t R = min((int64_t)P.s0 * G / 2, (int64_t)P.kcap);
     R = max(R, (int64_t)h - 1);
     R = min(R, nm);
+    int64_t t = 0;
+    if (D.keep && D.t0 > 0) {
+        t = D.t0;
+        R = D.R0;
+    }
     uint32_t epoch = 0;
     Tile T = partition(Q, R, G, gi, c0, h);
-    if (T.S > P.smax) {
+    if (T.S > P.smax || (D.keep && R > D.keep_r)) {
         pair_stop(D, gc, ST_WIDE);
         return true;
     }
@@ -607,7 +615,15 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     if (tid == 0)
         *S.n1 = 0;
     __syncthreads();
-    int64_t t = 0;
+    if (t > 0 && T.has) {
+        // round t - 1 of the tile and its halo from the keep buffer
+        const int64_t plo = max(-(t - 1), -n), phi = min(t - 1, m);
+        int32_t *dst = S.F[(t - 1) & 1];
+        for (int64_t d = T.a - h + tid; d < T.b + h; d += nt)
+            dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? D.keep[d + D.keep_r + 2] : NEG;
+    }
+    __syncthreads();
+    int64_t t_ep = t; // round of the last epoch change (or of the start)
     for (;;) {
         // ---------------------------------------------- stop / epoch checks
         if (tid == 0) {
@@ -625,7 +641,8 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             return true;
         if (stop == 2)
             return false;
-        const bool need_change = (t + h - 1 > R) && (R < nm);
+        const bool need_change =
+            ((t + h - 1 > R) && (R < nm)) || (can_suspend && t >= t_ep + P.sync_rounds);
         if (!T.has && !need_change) {
             // no tile: help open slides until the epoch changes or k is found
             uint64_t t0 = tid == 0 ? gtimer() : 0;
@@ -662,19 +679,26 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
                     __nanosleep(256);
             }
         }
-        if ((t + h - 1 > R) && (R < nm)) {
+        const bool grow = (t + h - 1 > R) && (R < nm);
+        if (grow || (can_suspend && t >= t_ep + P.sync_rounds)) {
             // ------------------------------------------ epoch change
+            // (a sync point of a time-sliced pair re-tiles at the same radius)
             const uint64_t te0 = clock64();
-            int64_t Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
-            if (t + h - 1 > Rn && Rn < nm) {
-                pair_stop(D, gc, ST_LIMIT);
-                return true;
-            }
-            // no further than the group's tiles hold
-            Rn = min(Rn, fit_radius(n, m, (int64_t)G * P.smax));
-            if (t + h - 1 > Rn && Rn < nm) {
-                pair_stop(D, gc, ST_WIDE);
-                return true;
+            int64_t Rn = R;
+            if (grow) {
+                Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
+                if (t + h - 1 > Rn && Rn < nm) {
+                    pair_stop(D, gc, ST_LIMIT);
+                    return true;
+                }
+                // no further than the group's tiles (and the keep buffer) hold
+                Rn = min(Rn, fit_radius(n, m, (int64_t)G * P.smax));
+                if (D.keep)
+                    Rn = min(Rn, D.keep_r);
+                if (t + h - 1 > Rn && Rn < nm) {
+                    pair_stop(D, gc, ST_WIDE);
+                    return true;
+                }
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
             if (T.has) {
@@ -683,6 +707,8 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
                     st_cg(buf + d + kc + 2, src[d - (T.a - h) + 1]);
             }
             if (leader) {
+                // the leader alone decides whether the launch leaves the pair here
+                gc->susp[(epoch + 1) & 1] = (can_suspend && gtimer() >= deadline) ? 1u : 0u;
                 gc->epoch_t = (uint32_t)t;
                 __threadfence();
                 st_release(&gc->epoch_req, epoch + 1);
@@ -694,6 +720,19 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             if (eb == 2)
                 return true; // k is known: the pair is over
             epoch++;
+            if (*(volatile uint32_t *)&gc->susp[epoch & 1]) {
+                // save round t - 1 of the band for the next launch, then leave
+                const int64_t plo = max(-(t - 1), -n), phi = min(t - 1, m);
+                for (int64_t d = plo + (int64_t)gi * nt + tid; d <= phi; d += (int64_t)G * nt)
+                    D.keep[d + D.keep_r + 2] = ld_cg(buf + d + kc + 2);
+                if (leader) {
+                    D.res[R_STATUS] = ST_SUSPENDED;
+                    D.res[R_RESUME_T] = (unsigned long long)t;
+                    D.res[R_RESUME_R] = (unsigned long long)Rn;
+                }
+                return true;
+            }
+            t_ep = t;
             R = Rn;
             T = partition(Q, R, G, gi, c0, h);
             if (T.S > P.smax) {
@@ -862,6 +901,7 @@ __device__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
 __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
 {
     const Smem S = carve(P);
+    const uint64_t deadline = gtimer() + P.budget_ns;
     int cls = 0;
     while (cls + 1 < P.ncls && (int)blockIdx.x >= P.cls_c0[cls + 1])
         cls++;
@@ -897,7 +937,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         if (q < 0)
             break;
         const PairDesc D = P.pairs[q];
-        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, iter, C);
+        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, iter, deadline, C);
         flush_counters(D, C, gi == 0);
         if (!ok)
             break;

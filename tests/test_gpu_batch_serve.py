@@ -129,6 +129,45 @@ def test_serving_matches_oracle_alone_and_mixed(orc):
     c.close()
 
 
+def test_serving_time_slices_wide_pairs(orc):
+    """Pairs whose band outgrows one CTA run on the tile kernel a slice per
+    engine step, their band frontiers saved and resumed between steps.
+    Small pairs submitted after a long pair finish before it, and every
+    result is exact: the long pair has disjoint alphabets (no character
+    matches, so the distance is max(n, m) after that many rounds), the
+    others are checked against the oracle."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    rng = np.random.default_rng(99)
+    n_long = 100_000
+    long_pair = (rng.integers(0, 4, n_long, dtype=np.uint8), rng.integers(4, 8, n_long, dtype=np.uint8))
+    heavy = W.make_pair(97, 500_000, 25_000, sigma=4)
+    small = [W.make_pair(98, 10_000, 10, sigma=4, extra=i) for i in range(16)]
+    want = [n_long] + list(orc.many("lv", [(p.A, p.B) for p in [heavy] + small]))
+    c = ed.Context(device=0, max_inflight=64)
+    try:
+        tickets = [ed.ed_submit(c.h, *long_pair), ed.ed_submit(c.h, heavy.A, heavy.B)]
+        time.sleep(0.02)  # the long pairs are on the device before the rest arrive
+        tickets += [ed.ed_submit(c.h, p.A, p.B) for p in small]
+        got, order = {}, []
+        t0 = time.time()
+        while len(got) < len(tickets):
+            for i, t in enumerate(tickets):
+                if i not in got:
+                    st, k = ed.ed_poll(c.h, t)
+                    if st == ed.ED_OK:
+                        got[i] = k
+                        order.append(i)
+            assert time.time() - t0 < 120, "serving did not finish"
+            time.sleep(0.0005)
+        assert [got[i] for i in range(len(tickets))] == want
+        # the small pairs did not wait for the long one
+        assert order.index(0) > max(order.index(i) for i in range(2, len(tickets)))
+        assert ed.ed_serve_counters(c.h)["slices"] >= 1
+    finally:
+        c.close()
+
+
 def test_poll_unknown_ticket(ctx):
     from paper_2306_17461_gb300 import binding as ed
 
