@@ -426,7 +426,6 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.smax = (int32_t)smax;
     P.h = h;
     P.s0 = s0;
-    P.t1_cap = 64;
     P.t2_cap = 4096;
     P.use_hash = jobs[0].TA != nullptr;
     std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
@@ -836,7 +835,6 @@ static int batch_launch(ed_ctx *ctx, std::vector<BatchPair> &hp, const std::vect
     Bg.W = BATCH_W;
     Bg.round_budget = 0;
     Bg.next = (uint32_t *)dnext.p;
-    Bg.t1_cap = 64;
     Bg.t2_cap = 8192;
     Bg.spin_ns = ctx->cfg.spin_limit_ns;
     const int occ = lv_batch_ctas_per_sm(BATCH_W);

@@ -178,7 +178,43 @@ __device__ __forceinline__ int64_t word_slide(const uint8_t *A, const uint8_t *B
     return -1;
 }
 
-// The 16-byte window part of slide_thread_w, from l bytes already equal.
+// The aligned 4-byte word holding A[x] and the one after it, and the same
+// for B[y]: at least five bytes from each start row whatever its
+// alignment.  The second word is loaded only while it still holds a byte of
+// the string (an aligned word holding a valid byte cannot fault); else 0.
+__device__ __forceinline__ void word_load2(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
+                                           int64_t x, int64_t y, uint2 &wa, uint2 &wb)
+{
+    const uintptr_t pa = (uintptr_t)(A + x) & ~(uintptr_t)3, pb = (uintptr_t)(B + y) & ~(uintptr_t)3;
+    wa.x = __ldg(reinterpret_cast<const uint32_t *>(pa));
+    wb.x = __ldg(reinterpret_cast<const uint32_t *>(pb));
+    wa.y = pa + 4 < (uintptr_t)(A + n) ? __ldg(reinterpret_cast<const uint32_t *>(pa + 4)) : 0u;
+    wb.y = pb + 4 < (uintptr_t)(B + m) ? __ldg(reinterpret_cast<const uint32_t *>(pb + 4)) : 0u;
+}
+
+// The LCP from (x, y) as far as the words of word_load2 decide it: the
+// matched length when a mismatch shows within them or `lim` is reached,
+// else -1 (every byte they hold matched; the slide goes on elsewhere).
+__device__ __forceinline__ int64_t word_slide2(const uint8_t *A, const uint8_t *B, int64_t x, int64_t y,
+                                               int64_t lim, uint2 wa, uint2 wb)
+{
+    if (lim <= 0)
+        return 0;
+    const uint32_t sa = (uint32_t)((uintptr_t)(A + x) & 3), sb = (uint32_t)((uintptr_t)(B + y) & 3);
+    const uint64_t va = (((uint64_t)wa.y << 32) | wa.x) >> (8 * sa);
+    const uint64_t vb = (((uint64_t)wb.y << 32) | wb.x) >> (8 * sb);
+    int64_t av = (int64_t)(8 - max(sa, sb));
+    if (av > lim)
+        av = lim;
+    const uint64_t mask = av >= 8 ? ~0ull : ((1ull << (8 * av)) - 1ull);
+    const uint64_t dif = (va ^ vb) & mask;
+    if (dif)
+        return (__ffsll((long long)dif) - 1) >> 3;
+    return av >= lim ? lim : -1;
+}
+
+// The 16-byte window part of slide_thread_w, from l bytes already equal:
+// four windows (64 bytes) per step, their loads in flight together.
 static __device__ __noinline__ int64_t slide_more(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
                                            int64_t x, int64_t y, int64_t l, int64_t lim, int64_t cap,
                                            bool *open)
@@ -186,17 +222,42 @@ static __device__ __noinline__ int64_t slide_more(const uint8_t *A, int64_t n, c
     *open = false;
     const int64_t stop = min(lim, cap);
     while (l < stop) {
-        const uint4 va = load16(A, n, x + l);
-        const uint4 vb = load16(B, m, y + l);
-        const int f = first_diff16(va, vb);
-        if (f < 16)
-            return min(l + f, lim);
-        l += 16;
+        uint4 va[4], vb[4];
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            if (l + 16 * w < stop) {
+                va[w] = load16(A, n, x + l + 16 * w);
+                vb[w] = load16(B, m, y + l + 16 * w);
+            }
+        }
+#pragma unroll
+        for (int w = 0; w < 4; w++) {
+            if (l + 16 * w < stop) {
+                const int f = first_diff16(va[w], vb[w]);
+                if (f < 16)
+                    return min(l + 16 * w + f, lim);
+            }
+        }
+        l = min(l + 64, stop);
     }
     if (l >= lim)
         return lim;
     *open = true;
     return l;
+}
+
+// Asks L2 for the 4 KiB of each string that follow rows x (of A) and y (of
+// B), one 128-byte line per lane of the calling warp: a diagonal that just
+// ended a long slide starts its next round there.  Only addresses inside
+// the strings are touched; a line never crosses a page.
+__device__ __forceinline__ void prefetch_next(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
+                                              int64_t x, int64_t y)
+{
+    const int64_t o = (int64_t)(threadIdx.x & 31) * 128;
+    if (x + o < n)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(A + x + o));
+    if (y + o < m)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(B + y + o));
 }
 
 __device__ __forceinline__ int64_t slide_thread(const uint8_t *A, int64_t n, const uint8_t *B,

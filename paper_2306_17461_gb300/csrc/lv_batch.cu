@@ -18,7 +18,7 @@ namespace edg {
 constexpr int BT = 256; // threads per batch CTA
 
 struct BSmem {
-    int32_t *f[2];   // frontiers, W + 3 entries each (index d + W/2 + 1)
+    int32_t *f0, *f1; // frontiers by round parity, W + 3 entries each (index d + W/2 + 1)
     int32_t *ld;     // open slides: diagonal (W + 1 entries)
     int *n1, *flag, *claim, *reach;
     uint32_t *err;   // self-check status of the round function
@@ -48,11 +48,13 @@ __device__ BSmem bcarve(int W)
     p += 256;
     S.ld = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (W + 1);
-    S.f[0] = reinterpret_cast<int32_t *>(p);
+    S.f0 = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (W + 3);
-    S.f[1] = reinterpret_cast<int32_t *>(p);
+    S.f1 = reinterpret_cast<int32_t *>(p);
     return S;
 }
+
+__device__ __forceinline__ int32_t *bfront(const BSmem S, int64_t r) { return (r & 1) ? S.f1 : S.f0; }
 
 // The whole CTA finishes one open slide: the first mismatch of
 // A[pos..lim_abs) vs B[pos+d..), 32 KiB per step with every load in flight.
@@ -72,7 +74,7 @@ __device__ __noinline__ int64_t cta_slide(const uint8_t *A, int64_t n, const uin
 // One warp's attempt at an open slide, out of line so that the round loop
 // keeps its registers: the first mismatch within cap bytes of the start, or
 // *open when there is none.
-__device__ __noinline__ int64_t warp_slide(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int64_t c,
+__device__ __forceinline__ int64_t warp_slide(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int64_t c,
                                            int64_t d, int64_t len, int64_t cap, bool *open)
 {
     return slide_warp(A, n, B, m, c, c + d, 0, len, cap, open);
@@ -113,13 +115,13 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
         // restore the resident frontier (round t0) or start at round 0
         const int64_t t0 = Pr.t;
         for (int i = tid; i < Bg.W + 3; i += nt) {
-            S.f[0][i] = NEG;
-            S.f[1][i] = NEG;
+            S.f0[i] = NEG;
+            S.f1[i] = NEG;
         }
         __syncthreads();
         if (t0 >= 0) {
             const int32_t *src = Pr.front;
-            int32_t *dst = S.f[t0 & 1];
+            int32_t *dst = bfront(S, t0);
             for (int i = tid; i < Bg.W + 3; i += nt)
                 dst[i] = src[i];
         }
@@ -147,8 +149,8 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
                 break;
             }
             rounds_here++;
-            const int32_t *prev = S.f[(t - 1) & 1];
-            int32_t *cur = S.f[t & 1];
+            const int32_t *prev = bfront(S, t - 1);
+            int32_t *cur = bfront(S, t);
             RoundArgs RA;
             RA.A = A;
             RA.B = B;
@@ -162,12 +164,11 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
             RA.tau = t;
             RA.a = lo;
             RA.b = hi + 1;
-            RA.t1_cap = Bg.t1_cap;
             RA.n1 = S.n1;
             RA.open = S.ld;
             RA.err = S.err;
             RA.diag = S.diag;
-            const RoundCount rc = tile_round(RA);
+            const RoundCount rc = tile_round<4>(RA);
             slide += rc.slide;
             mism += rc.mism;
             __syncthreads();
@@ -184,6 +185,8 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
                     const int64_t lim = c + min(n - c, m - c - d);
                     bool open;
                     const int64_t l = warp_slide(A, n, B, m, c, d, lim - c, Bg.t2_cap, &open);
+                    if (!open)
+                        prefetch_next(A, n, B, m, c + l, c + l + d);
                     if (lane == 0) {
                         if (!open) {
                             cur[d - off] = (int32_t)(c + l);
@@ -201,6 +204,8 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
                     const int64_t c = start_row(prev, off, d, t, n, m);
                     const int64_t lim = c + min(n - c, m - c - d);
                     const int64_t row = cta_slide(A, n, B, m, d, c, lim, S.smin);
+                    if (tid < 32)
+                        prefetch_next(A, n, B, m, row, row + d);
                     if (tid == 0) {
                         cur[d - off] = (int32_t)row;
                         slide += row - c;
@@ -246,7 +251,7 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
         } else {
             // save the last completed round (t - 1) as the resident frontier;
             // its furthest row tells the host how far along the pair is
-            const int32_t *src = S.f[(t - 1) & 1];
+            const int32_t *src = bfront(S, t - 1);
             int r = 0;
             for (int i = tid; i < Bg.W + 3; i += nt) {
                 Pr.front[i] = src[i];

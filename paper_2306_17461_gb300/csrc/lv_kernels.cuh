@@ -12,11 +12,11 @@ constexpr uint32_t ST_LIMIT = 7;  // the round cap was reached
 constexpr uint32_t ST_WIDE = 8;   // per pair: the band outgrew its group's tiles
 constexpr uint32_t ST_SUSPENDED = 9; // per pair: budget spent, frontier saved to keep
 
-constexpr int CTA_THREADS = 512;   // threads of a tile CTA
+constexpr int CTA_THREADS = 256;   // threads of a tile CTA (up to 255 registers each)
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
 constexpr int HMAX = 16;           // rounds per temporal block, at most
 constexpr int CHUNK_UNROLL = 8;
-constexpr int CHUNK_BYTES = CTA_THREADS * 16 * CHUNK_UNROLL; // 64 KiB per claim
+constexpr int CHUNK_BYTES = 64 * 1024; // bytes of one job-slot claim
 constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
 constexpr uint32_t CLAIM_CLOSED = 0xffffffffu;
 constexpr int MAX_CLS = 12;        // group-size classes of one tile launch
@@ -119,7 +119,6 @@ struct LvArgs {
     int32_t smax;         // tile width capacity (shared memory)
     int32_t h;            // rounds per temporal block (1..HMAX)
     int32_t s0;           // initial tile width
-    int32_t t1_cap;       // bytes one thread examines before escalating
     int32_t t2_cap;       // bytes one warp examines before escalating
     int32_t use_hash;
     uint64_t pow2[62];    // p^(2^j) mod 2^61-1 (hash LCP)
@@ -157,7 +156,7 @@ struct BatchArgs {
     int32_t W;            // band capacity per pair (even)
     int32_t round_budget; // rounds per launch per pair (<=0: unlimited)
     uint32_t *next;       // work-queue head
-    int32_t t1_cap, t2_cap;
+    int32_t t2_cap;
     uint64_t spin_ns;
     uint32_t *error;
 };

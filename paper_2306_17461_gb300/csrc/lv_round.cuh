@@ -6,22 +6,21 @@
 //     c      = max(L_{t-1}[d-1], L_{t-1}[d] + 1, L_{t-1}[d+1] + 1), clamped
 //              to the diagonal's last cell min(n, m - d)
 //     L_t[d] = c + LCP(A[c..], B[c+d..])
-// The slide is taken here as far as one thread goes cheaply (the aligned
-// words at the start row, then 16-byte windows up to t1_cap bytes); longer
-// slides are listed for the caller.
+// The slide is taken here as far as the aligned words at the start row
+// decide it (one load per string and word, all of a thread's diagonals in
+// flight together); slides that match all the bytes those words hold are
+// listed for the caller, which continues them a warp each.
 #pragma once
 #include "ed_device.cuh"
 
 namespace edg {
 
-constexpr int DPT = 4; // diagonals per thread per batch
 struct RoundArgs {
     const uint8_t *A, *B;
     int64_t n, m;
     const int32_t *prev;     // round tau-1, indexed d - off
     int32_t *cur;            // round tau
     int64_t off, lo, hi, tau, a, b;
-    int t1_cap;
     int *n1;
     int32_t *open;           // diagonals whose slide is still open
     uint32_t *err;           // launch status word (self-check records)
@@ -45,23 +44,23 @@ __device__ __forceinline__ int64_t start_row(const int32_t *prev, int64_t off, i
 }
 
 // One round over diagonals [lo, hi] of the tile (strided over the CTA): the
-// start row, then the per-thread slide.  DPT diagonals per thread are
-// handled together so that their first loads are in flight together.
-// Diagonals whose slide is still open after t1_cap bytes are listed; the
-// list holds one entry per computed diagonal at most, so it cannot fill.
-// Counts only diagonals of [a, b).
+// start row, then the word slide.  DPT diagonals per thread are handled
+// together so that their loads are in flight together.  Diagonals whose
+// slide is still open are listed; the list holds one entry per computed
+// diagonal at most, so it cannot fill.  Counts only diagonals of [a, b).
+template <int DPT> // diagonals per thread per batch
 __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
 {
     RoundCount out = {0, 0};
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int64_t base = R.lo; base <= R.hi; base += (int64_t)nt * DPT) {
         int64_t c[DPT];
-        uint32_t wa[DPT], wb[DPT];
+        uint2 wa[DPT], wb[DPT];
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
             const int64_t d = base + (int64_t)u * nt + tid;
             c[u] = 0;
-            wa[u] = wb[u] = 0;
+            wa[u] = wb[u] = make_uint2(0u, 0u);
             if (d <= R.hi) {
                 c[u] = start_row(R.prev, R.off, d, R.tau, R.n, R.m);
                 if (c[u] < 0 || c[u] + d < 0) {
@@ -78,7 +77,7 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
                     }
                     c[u] = -1; // skipped below: no load at a bad row
                 } else if (min(R.n - c[u], R.m - c[u] - d) > 0) {
-                    word_load(R.A, R.B, c[u], c[u] + d, wa[u], wb[u]);
+                    word_load2(R.A, R.n, R.B, R.m, c[u], c[u] + d, wa[u], wb[u]);
                 }
             }
         }
@@ -88,12 +87,8 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
             if (d <= R.hi && c[u] >= 0) {
                 const int64_t cc = c[u];
                 const int64_t full = min(R.n - cc, R.m - cc - d);
-                bool op = false;
-                int64_t av = 0;
-                int64_t l = word_slide(R.A, R.B, cc, cc + d, full, wa[u], wb[u], &av);
-                if (l < 0) // rare: the words matched; 16-byte windows, out of line
-                    l = slide_more(R.A, R.n, R.B, R.m, cc, cc + d, av, full, R.t1_cap, &op);
-                if (!op) {
+                const int64_t l = word_slide2(R.A, R.B, cc, cc + d, full, wa[u], wb[u]);
+                if (l >= 0) {
                     R.cur[d - R.off] = (int32_t)(cc + l);
                     if (d >= R.a && d < R.b) {
                         out.slide += l;

@@ -20,11 +20,13 @@
 //    its two neighbours through global memory and a per-CTA release flag.
 //    There is no grid-wide barrier per round, only neighbour waits every h
 //    rounds.
-//  * Slides: one thread compares the leading 4-byte words (several
-//    diagonals' loads in flight together), then 16-byte windows; slides
-//    still open after t1_cap bytes go to one warp each (ballot / first set
-//    bit over 512-byte steps) or, when few, straight to the whole CTA, which
-//    scans 64 KiB per step with every load in flight.  A slide still open
+//  * Slides: one thread compares the two aligned 4-byte words at each start
+//    row (at least five bytes; several diagonals' loads in flight
+//    together); slides that match all of them go to one warp each (ballot /
+//    first set bit over 2 KiB steps, prefetching the next 4 KiB into L2 when
+//    done, where the next round starts), then, if still open after t2_cap
+//    bytes, to the whole CTA, which scans 64 KiB per step with every load in
+//    flight.  A slide still open
 //    after LOCAL_STEPS such steps becomes a job in the CTA's job slot: its
 //    64 KiB chunks are claimed by atomicAdd by the owner and by every CTA
 //    that is waiting on a neighbour or has no tile; the first mismatch is the
@@ -43,6 +45,10 @@ constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owne
 struct Counters {
     unsigned long long slide = 0, mism = 0, hashq = 0, coll = 0, longs = 0, blocks = 0;
     unsigned long long tm[4] = {0, 0, 0, 0};
+};
+// What one call of open_slides adds to the counters.
+struct SlideCounts {
+    unsigned long long slide, mism, hashq, coll, longs;
 };
 
 // ------------------------------------------------------------------ hash
@@ -172,8 +178,10 @@ __device__ __noinline__ void wait_failed(const LvArgs &P, unsigned long long sit
     }
 }
 
+// Kept in registers: every function takes it by value (no address taken,
+// no array member indexed at run time).
 struct Smem {
-    int32_t *F[2];      // tile + halo frontier, smax + 2*HMAX + 2 entries each
+    int32_t *F0, *F1;   // tile + halo frontier, smax + 2*HMAX + 2 entries each
     int32_t *ld;        // open slides: diagonal (lcap entries)
     int *n1;
     int *bc;            // 8 broadcast words
@@ -205,7 +213,7 @@ __device__ __forceinline__ int64_t claim_chunk(JobSlot *sl)
 
 // Scan (or skip) claimed chunk c of slot sl with the whole CTA, lower the
 // job's result, answer the claim.
-__device__ __noinline__ void serve_claim(const Smem &S, JobSlot *sl, int64_t c)
+__device__ __noinline__ void serve_claim(const Smem S, JobSlot *sl, int64_t c)
 {
     // the slot is rewritten for every job: read it past the L1
     const uint8_t *A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
@@ -248,7 +256,7 @@ __device__ __noinline__ void serve_claim(const Smem &S, JobSlot *sl, int64_t c)
 
 // Help one open job of any CTA (whole CTA).  Returns true if a claim was
 // made.
-__device__ bool help_one(const LvArgs &P, const Smem &S)
+__device__ bool help_one(const LvArgs &P, const Smem S)
 {
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -299,8 +307,8 @@ __device__ bool help_one(const LvArgs &P, const Smem &S)
 // job in the CTA's slot, claimed chunk by chunk by the CTA and by helpers;
 // the CTA then closes the job and waits for the claims still running.
 // Returns the first mismatch offset, or lim.
-__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const Pair &Q, int64_t x,
-                                           int64_t y, int64_t lim, Counters &C)
+__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const Pair Q, int64_t x,
+                                           int64_t y, int64_t lim)
 {
     const int tid = threadIdx.x;
     int64_t off = 0;
@@ -313,7 +321,8 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const
     }
     if (off >= lim)
         return lim;
-    C.longs++;
+    // (the caller counts this as a job-slot slide: lim and the result both
+    // reach LOCAL_STEPS chunks)
     JobSlot *sl = &P.slots[blockIdx.x];
     const int64_t rest = lim - off;
     const uint32_t nch = (uint32_t)((rest + CHUNK_BYTES - 1) / CHUNK_BYTES);
@@ -378,7 +387,7 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem &S, const
 // group's k became known meanwhile (the epoch-change barrier: CTAs that
 // have seen k leave the pair without arriving).
 __device__ int group_barrier(const LvArgs &P, GroupCtl *gc, uint32_t *count, uint32_t *gen_p, int G,
-                             bool abandon, const Smem &S)
+                             bool abandon, const Smem S)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -416,7 +425,7 @@ __device__ int group_barrier(const LvArgs &P, GroupCtl *gc, uint32_t *count, uin
     return ok;
 }
 
-__device__ bool group_sync(const LvArgs &P, GroupCtl *gc, int G, const Smem &S)
+__device__ bool group_sync(const LvArgs &P, GroupCtl *gc, int G, const Smem S)
 {
     return group_barrier(P, gc, &gc->bar_count, &gc->bar_gen, G, false, S) == 1;
 }
@@ -427,6 +436,9 @@ size_t lv_tiles_smem_bytes(int smax, int h)
     // two frontier buffers and the open-slide list, each smax + 2*HMAX + 2
     return 128 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2);
 }
+
+// The frontier of round r (buffers alternate by parity).
+__device__ __forceinline__ int32_t *frontier(const Smem S, int64_t r) { return (r & 1) ? S.F1 : S.F0; }
 
 __device__ Smem carve(const LvArgs &P)
 {
@@ -441,9 +453,9 @@ __device__ Smem carve(const LvArgs &P)
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * S.lcap;
-    S.F[0] = reinterpret_cast<int32_t *>(p);
+    S.F0 = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (P.smax + 2 * HMAX + 2);
-    S.F[1] = reinterpret_cast<int32_t *>(p);
+    S.F1 = reinterpret_cast<int32_t *>(p);
     S.err = &P.ctl->error;
     S.diag = P.ctl->diag;
     return S;
@@ -457,7 +469,7 @@ struct Tile {
     int left, right; // neighbour CTA (grid index) or -1
 };
 
-__device__ Tile partition(const Pair &Q, int64_t R, int G, int gi, int c0, int h)
+__device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int gi, int c0, int h)
 {
     Tile T;
     T.lo_all = max(-R, -Q.n);
@@ -499,12 +511,11 @@ __device__ __forceinline__ void open_bounds(const LvArgs &P, const Pair &Q, cons
 // Open slides of one round: one warp each (t2_cap bytes, which finishes
 // most of them in one or two 2 KiB steps); what is still open after that
 // goes to the whole CTA and, if longer still, to the job slots
-// (long_slide).  The per-thread bytes already compared are simply compared
-// again (at most t1_cap).
-__device__ __noinline__ void open_slides(const LvArgs &P, const Smem &S, const Pair &Q, const int32_t *prev,
-                                         int32_t *cur, int64_t off, int64_t tau, int64_t a, int64_t b, int n1,
-                                         Counters &C)
+// (long_slide).  The few bytes the words showed equal are compared again.
+__device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S, const Pair Q, const int32_t *prev,
+                                             int32_t *cur, int64_t off, int64_t tau, int64_t a, int64_t b, int n1)
 {
+    Counters C; // this call's counts, added by the caller
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     {
         for (int j = warp; j < n1; j += nw) {
@@ -517,6 +528,8 @@ __device__ __noinline__ void open_slides(const LvArgs &P, const Smem &S, const P
             lim = __shfl_sync(0xffffffffu, lim, 0);
             bool open;
             const int64_t l = slide_warp(Q.A, Q.n, Q.B, Q.m, c, c + d, 0, lim - c, P.t2_cap, &open);
+            if (!open)
+                prefetch_next(Q.A, Q.n, Q.B, Q.m, c + l, c + l + d);
             if (lane == 0) {
                 if (!open) {
                     cur[d - off] = (int32_t)finish_slide(Q, c, d, c + l, lim, own, C);
@@ -540,11 +553,16 @@ __device__ __noinline__ void open_slides(const LvArgs &P, const Smem &S, const P
         __syncthreads();
         const int64_t c = S.bcl[2], lim = S.bcl[3];
         __syncthreads();
-        const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c, C);
+        const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c);
+        if (lim - c > (int64_t)LOCAL_STEPS * CHUNK_BYTES && rr >= (int64_t)LOCAL_STEPS * CHUNK_BYTES)
+            C.longs++;
+        if (tid < 32)
+            prefetch_next(Q.A, Q.n, Q.B, Q.m, c + rr, c + rr + d);
         if (tid == 0)
             cur[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
     }
     __syncthreads();
+    return SlideCounts{C.slide, C.mism, C.hashq, C.coll, C.longs};
 }
 
 // The largest epoch radius whose band [max(-R, -n), min(R, m)] fits in
@@ -574,7 +592,7 @@ __device__ void pair_stop(const PairDesc &D, GroupCtl *gc, uint32_t status)
 
 // Runs one pair on the group; kc is the radius its re-tiling buffers hold.
 // Returns false if the launch must stop.
-__device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, GroupCtl *gc, int gi, int G,
+__device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const PairDesc &D, GroupCtl *gc, int gi, int G,
                          int c0, int32_t *gfb, int64_t kc, unsigned long long iter, uint64_t deadline,
                          Counters &C)
 {
@@ -609,8 +627,8 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         return true;
     }
     for (int i = tid; i < P.smax + 2 * HMAX + 2; i += nt) {
-        S.F[0][i] = NEG;
-        S.F[1][i] = NEG;
+        S.F0[i] = NEG;
+        S.F1[i] = NEG;
     }
     if (tid == 0)
         *S.n1 = 0;
@@ -618,7 +636,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     if (t > 0 && T.has) {
         // round t - 1 of the tile and its halo from the keep buffer
         const int64_t plo = max(-(t - 1), -n), phi = min(t - 1, m);
-        int32_t *dst = S.F[(t - 1) & 1];
+        int32_t *dst = frontier(S, t - 1);
         for (int64_t d = T.a - h + tid; d < T.b + h; d += nt)
             dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? D.keep[d + D.keep_r + 2] : NEG;
     }
@@ -702,7 +720,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
             if (T.has) {
-                const int32_t *src = S.F[(t - 1) & 1];
+                const int32_t *src = frontier(S, t - 1);
                 for (int64_t d = T.a + tid; d < T.b; d += nt)
                     st_cg(buf + d + kc + 2, src[d - (T.a - h) + 1]);
             }
@@ -741,7 +759,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             }
             if (T.has) {
                 const int64_t plo = max(-(t - 1), -n), phi = min(t - 1, m);
-                int32_t *dst = S.F[(t - 1) & 1];
+                int32_t *dst = frontier(S, t - 1);
                 for (int64_t d = T.a - h + tid; d < T.b + h; d += nt)
                     dst[d - (T.a - h) + 1] = (d >= plo && d <= phi) ? ld_cg(buf + d + kc + 2) : NEG;
             }
@@ -758,7 +776,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             const int64_t tau = t + r;
             const int64_t ra = a - h + 1 + r, rb = b + h - 1 - r; // computed range [ra, rb)
             const int64_t blo = max(-tau, -n), bhi = min(tau, m);
-            int32_t *cur = S.F[tau & 1];
+            int32_t *cur = frontier(S, tau);
             // outside the band: minus infinity
             for (int64_t d = ra + tid; d < rb; d += nt)
                 if (d < blo || d > bhi)
@@ -768,7 +786,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             RA.B = Q.B;
             RA.n = n;
             RA.m = m;
-            RA.prev = S.F[(tau - 1) & 1];
+            RA.prev = frontier(S, tau - 1);
             RA.cur = cur;
             RA.off = off;
             RA.lo = max(ra, blo);
@@ -776,12 +794,11 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             RA.tau = tau;
             RA.a = a;
             RA.b = b;
-            RA.t1_cap = P.t1_cap;
             RA.n1 = S.n1;
             RA.open = S.ld;
             RA.err = &P.ctl->error;
             RA.diag = P.ctl->diag;
-            const RoundCount rc = tile_round(RA);
+            const RoundCount rc = tile_round<2048 / CTA_THREADS>(RA);
             C.slide += rc.slide;
             C.mism += rc.mism;
             __syncthreads();
@@ -789,7 +806,12 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
             C.tm[0] += tr1 - tr0;
             const int n1 = *S.n1;
             if (n1 > 0) {
-                open_slides(P, S, Q, S.F[(tau - 1) & 1], cur, off, tau, a, b, n1, C);
+                const SlideCounts oc = open_slides(P, S, Q, frontier(S, tau - 1), cur, off, tau, a, b, n1);
+                C.slide += oc.slide;
+                C.mism += oc.mism;
+                C.hashq += oc.hashq;
+                C.coll += oc.coll;
+                C.longs += oc.longs;
                 if (tid == 0)
                     *S.n1 = 0;
                 C.tm[1] += clock64() - tr1;
@@ -816,7 +838,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
         // ---------------------------------------------- halo exchange
         const uint64_t tw0 = clock64();
         const int parity = (int)((t / h) & 1);
-        const int32_t *last = S.F[(t - 1) & 1];
+        const int32_t *last = frontier(S, t - 1);
         int32_t *hl = halo_ptr(P, blockIdx.x, parity, 0), *hr = halo_ptr(P, blockIdx.x, parity, 1);
         if (tid < h) {
             const int64_t dl = a + tid, dr = b - h + tid;
@@ -860,7 +882,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
                 break;
             help_one(P, S);
         }
-        int32_t *edge = S.F[(t - 1) & 1];
+        int32_t *edge = frontier(S, t - 1);
         if (tid < h) {
             edge[a - h + tid - off] = T.left >= 0 ? ld_cg(halo_ptr(P, T.left, parity, 1) + tid) : NEG;
             edge[b + tid - off] = T.right >= 0 ? ld_cg(halo_ptr(P, T.right, parity, 0) + tid) : NEG;
@@ -870,7 +892,7 @@ __device__ bool run_pair(const LvArgs &P, const Smem &S, const PairDesc &D, Grou
     }
 }
 
-__device__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
+__device__ __forceinline__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
 {
     unsigned long long v[6] = {C.slide, C.mism, C.hashq, C.coll, C.longs, C.blocks};
     for (int o = 16; o; o >>= 1)
