@@ -247,7 +247,8 @@ def run_single(args, D: Dist):
     for i, k, st in recs:
         d = per.setdefault(i, {"k": k, "planted": pairs[i].edits, "n": int(pairs[i].A.size),
                                "ms": [], "ext": st["extensions"], "compared_bytes": st["compared_bytes"],
-                               "long_slides": st["long_slides"], "wide_rounds": st["wide_rounds"],
+                               "long_slides": st["long_slides"], "open_slides": st["open_slides"],
+                               "wide_rounds": st["wide_rounds"],
                                "phase_ms": [round(x, 3) for x in st["phase_ms"]]})
         d["ms"].append(st["kernel_ms"])
     for d in per.values():

@@ -75,6 +75,8 @@ typedef struct {
     uint64_t slide_chars;    /* sum over extensions of the LCP length */
     uint64_t compared_bytes; /* 2 * (slide_chars + mismatching compares) */
     uint64_t long_slides;    /* slides handed to the job slots (helped) */
+    uint64_t open_slides;    /* slides the start-row words did not finish
+                                (continued by a warp), tile kernel only */
     uint64_t wide_rounds;    /* rounds run in temporal blocks */
     uint64_t hash_queries;   /* LCP queries answered by the hash search */
     uint64_t hash_collisions;/* hash answers refuted by the direct check */

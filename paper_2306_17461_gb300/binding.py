@@ -52,6 +52,7 @@ class ed_stats(ctypes.Structure):
         ("slide_chars", ctypes.c_uint64),
         ("compared_bytes", ctypes.c_uint64),
         ("long_slides", ctypes.c_uint64),
+        ("open_slides", ctypes.c_uint64),
         ("wide_rounds", ctypes.c_uint64),
         ("hash_queries", ctypes.c_uint64),
         ("hash_collisions", ctypes.c_uint64),

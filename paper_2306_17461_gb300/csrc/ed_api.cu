@@ -482,6 +482,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
         ctx->last.slide_chars += R[R_SLIDE];
         ctx->last.compared_bytes += 2ull * (R[R_SLIDE] + R[R_MISMATCH]);
         ctx->last.long_slides += R[R_LONG];
+        ctx->last.open_slides += R[R_OPEN];
         ctx->last.wide_rounds += R[R_WIDE] * (uint64_t)h;
         ctx->last.hash_queries += R[R_HASHQ];
         ctx->last.hash_collisions += R[R_HASHCOLL];
@@ -961,6 +962,7 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
         keep.kernel_ms += ctx->last.kernel_ms;
         keep.kernel_launches += ctx->last.kernel_launches;
         keep.long_slides += ctx->last.long_slides;
+        keep.open_slides += ctx->last.open_slides;
         keep.wide_rounds += ctx->last.wide_rounds;
     }
     ctx->last = keep;

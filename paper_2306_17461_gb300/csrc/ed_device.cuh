@@ -59,6 +59,19 @@ __device__ __forceinline__ uint4 ld_blk(const uint8_t *base, int64_t len, uintpt
     return make_uint4(0u, 0u, 0u, 0u);
 }
 
+// Branch-free form of ld_blk for len > 0, so that a thread's loads all
+// issue before any is used: a block that does not overlap the string is
+// replaced by the block holding the string's last byte (always valid).
+// Its bytes lie outside the window asked for and are masked by the
+// caller's bound like any byte past the string.
+__device__ __forceinline__ uint4 ld_blk_nb(const uint8_t *base, int64_t len, uintptr_t blk)
+{
+    const uintptr_t b = (uintptr_t)base;
+    const bool in = blk + 16 > b && blk < b + (uintptr_t)len;
+    const uintptr_t safe = (b + (uintptr_t)len - 1) & ~(uintptr_t)15;
+    return __ldg(reinterpret_cast<const uint4 *>(in ? blk : safe));
+}
+
 // 16 bytes of the 32-byte concatenation lo|hi starting at byte s (0..15).
 __device__ __forceinline__ uint4 shift_bytes(uint4 lo, uint4 hi, uint32_t s)
 {
@@ -289,21 +302,26 @@ __device__ __forceinline__ int64_t slide_warp(const uint8_t *A, int64_t n, const
     const int64_t stop = min(lim, l0 + cap);
     *open = false;
     for (int64_t base = l0; base < stop; base += 512 * UNROLL) {
-        uint4 va[UNROLL], vb[UNROLL];
+        // every aligned block first (windows past lim read a valid block and
+        // are ignored below), then the compares
+        uint4 alo[UNROLL], ahi[UNROLL], blo[UNROLL], bhi[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
-            const int64_t o = base + u * 512 + lane * 16;
-            if (o < lim) {
-                va[u] = load16(A, n, x + o);
-                vb[u] = load16(B, m, y + o);
-            }
+            const int64_t o = min(base + u * 512 + lane * 16, lim - 1);
+            const uintptr_t pa = ((uintptr_t)(A + x + o)) & ~(uintptr_t)15;
+            const uintptr_t pb = ((uintptr_t)(B + y + o)) & ~(uintptr_t)15;
+            alo[u] = ld_blk_nb(A, n, pa);
+            ahi[u] = ld_blk_nb(A, n, pa + 16);
+            blo[u] = ld_blk_nb(B, m, pb);
+            bhi[u] = ld_blk_nb(B, m, pb + 16);
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
             const int64_t o = base + u * 512 + lane * 16;
             int64_t cand = -1;
             if (o < lim) {
-                const int f = first_diff16(va[u], vb[u]);
+                const uint32_t sa = (uint32_t)((uintptr_t)(A + x + o) & 15), sb = (uint32_t)((uintptr_t)(B + y + o) & 15);
+                const int f = first_diff16(shift_bytes(alo[u], ahi[u], sa), shift_bytes(blo[u], bhi[u], sb));
                 if (f < 16 || o + 16 >= lim)
                     cand = min(o + f, lim);
             }
@@ -335,20 +353,26 @@ __device__ __forceinline__ int64_t cta_scan(const uint8_t *A, int64_t n, const u
     __syncthreads();
     int64_t best = -1;
     for (int64_t base = 0; base < len && best < 0; base += (int64_t)nt * 16 * UNROLL) {
-        uint4 va[UNROLL], vb[UNROLL];
+        // every aligned block first (windows past len read a valid block and
+        // are ignored below), then the compares
+        uint4 alo[UNROLL], ahi[UNROLL], blo[UNROLL], bhi[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
-            const int64_t o = base + ((int64_t)u * nt + tid) * 16;
-            if (o < len) {
-                va[u] = load16(A, n, x + off + o);
-                vb[u] = load16(B, m, y + off + o);
-            }
+            const int64_t o = min(base + ((int64_t)u * nt + tid) * 16, len - 1);
+            const uintptr_t pa = ((uintptr_t)(A + x + off + o)) & ~(uintptr_t)15;
+            const uintptr_t pb = ((uintptr_t)(B + y + off + o)) & ~(uintptr_t)15;
+            alo[u] = ld_blk_nb(A, n, pa);
+            ahi[u] = ld_blk_nb(A, n, pa + 16);
+            blo[u] = ld_blk_nb(B, m, pb);
+            bhi[u] = ld_blk_nb(B, m, pb + 16);
         }
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
             const int64_t o = base + ((int64_t)u * nt + tid) * 16;
             if (best < 0 && o < len) {
-                const int f = first_diff16(va[u], vb[u]);
+                const uint32_t sa = (uint32_t)((uintptr_t)(A + x + off + o) & 15),
+                               sb = (uint32_t)((uintptr_t)(B + y + off + o) & 15);
+                const int f = first_diff16(shift_bytes(alo[u], ahi[u], sa), shift_bytes(blo[u], bhi[u], sb));
                 if (f < 16 && o + f < len)
                     best = off + o + f;
             }

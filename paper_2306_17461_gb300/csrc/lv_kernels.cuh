@@ -94,7 +94,8 @@ enum {
     R_T0 = 8,
     R_RESUME_T = 14,  // suspended: the round to start from, and the radius
     R_RESUME_R = 15,
-    R_COUNT = 16
+    R_OPEN = 16,      // slides continued by a warp (own diagonals)
+    R_COUNT = 17
 };
 
 // The CTAs of a tile launch are cut into groups by class: class c has

@@ -43,12 +43,12 @@ constexpr int LOCAL_STEPS = 4;            // 64 KiB steps the owner takes alone
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
 struct Counters {
-    unsigned long long slide = 0, mism = 0, hashq = 0, coll = 0, longs = 0, blocks = 0;
+    unsigned long long slide = 0, mism = 0, hashq = 0, coll = 0, longs = 0, blocks = 0, opens = 0;
     unsigned long long tm[4] = {0, 0, 0, 0};
 };
 // What one call of open_slides adds to the counters.
 struct SlideCounts {
-    unsigned long long slide, mism, hashq, coll, longs;
+    unsigned long long slide, mism, hashq, coll, longs, opens;
 };
 
 // ------------------------------------------------------------------ hash
@@ -522,8 +522,10 @@ __device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S
             const int64_t d = S.ld[j];
             const bool own = d >= a && d < b;
             int64_t c = 0, lim = 0;
-            if (lane == 0)
+            if (lane == 0) {
                 open_bounds(P, Q, prev, off, tau, d, &c, &lim, C, own);
+                C.opens += own;
+            }
             c = __shfl_sync(0xffffffffu, c, 0);
             lim = __shfl_sync(0xffffffffu, lim, 0);
             bool open;
@@ -562,7 +564,21 @@ __device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S
             cur[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
     }
     __syncthreads();
-    return SlideCounts{C.slide, C.mism, C.hashq, C.coll, C.longs};
+    return SlideCounts{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens};
+}
+
+// Whether a CTA that is about to compute round t leaves the pair.  Once k
+// is known every CTA leaves at once, except with a frontier dump: a CTA may
+// lag its neighbours by a few blocks, so it first computes every round up
+// to k for its tile (those rounds lie in blocks that the owner of d = m - n
+// already ran at the same radius: no epoch change is needed, and its
+// neighbours have published their edges for them).
+__device__ __forceinline__ bool pair_over(const PairDesc &D, GroupCtl *gc, int64_t t)
+{
+    const unsigned long long v = *(volatile unsigned long long *)&gc->done_k;
+    if (v == ~0ull)
+        return false;
+    return !D.dump || v == DONE_STOPPED || (unsigned long long)t > v;
 }
 
 // The largest epoch radius whose band [max(-R, -n), min(R, m)] fits in
@@ -646,7 +662,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         // ---------------------------------------------- stop / epoch checks
         if (tid == 0) {
             int st = 0;
-            if (*(volatile unsigned long long *)&gc->done_k != ~0ull)
+            if (pair_over(D, gc, t))
                 st = 1;
             else if (ld_acquire(&P.ctl->error) != 0)
                 st = 2;
@@ -812,6 +828,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 C.hashq += oc.hashq;
                 C.coll += oc.coll;
                 C.longs += oc.longs;
+                C.opens += oc.opens;
                 if (tid == 0)
                     *S.n1 = 0;
                 C.tm[1] += clock64() - tr1;
@@ -859,7 +876,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 const bool rok = T.right < 0 || ld_acquire_u64(&P.ctl->flags[T.right]) >= want;
                 if (lok && rok)
                     st = 3;
-                else if (*(volatile unsigned long long *)&gc->done_k != ~0ull)
+                else if (pair_over(D, gc, t))
                     st = 1;
                 else if (ld_acquire(&P.ctl->error) != 0)
                     st = 2;
@@ -894,11 +911,12 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
 
 __device__ __forceinline__ void flush_counters(const PairDesc &D, Counters &C, bool first_cta)
 {
-    unsigned long long v[6] = {C.slide, C.mism, C.hashq, C.coll, C.longs, C.blocks};
+    unsigned long long v[7] = {C.slide, C.mism, C.hashq, C.coll, C.longs, C.blocks, C.opens};
     for (int o = 16; o; o >>= 1)
-        for (int i = 0; i < 6; i++)
+        for (int i = 0; i < 7; i++)
             v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
     if ((threadIdx.x & 31) == 0) {
+        if (v[6]) atomicAdd(&D.res[R_OPEN], v[6]);
         if (v[0]) atomicAdd(&D.res[R_SLIDE], v[0]);
         if (v[1]) atomicAdd(&D.res[R_MISMATCH], v[1]);
         if (v[2]) atomicAdd(&D.res[R_HASHQ], v[2]);
