@@ -30,6 +30,7 @@ namespace {
 constexpr int64_t MAX_LEN = (1ll << 31) - 64;
 constexpr uint64_t Q61H = (1ull << 61) - 1;
 constexpr int BATCH_W = 4096; // band capacity of one batch CTA
+constexpr int START_TILE = 2048; // diagonals per CTA a single pair starts with
 
 // host mod 2^61-1 (exact 128-bit product), for the hash base powers
 uint64_t hmul(uint64_t a, uint64_t b)
@@ -129,9 +130,13 @@ struct TileJob {
     int64_t dump_tmax;
     int G;       // CTAs of the group the pair runs on (1 .. grid)
     double cost; // estimated run time (any unit), to share CTAs among classes
-    // resident frontier for time slicing (serving), or null
+    // resident frontier (time slicing, resuming on wider tiles), or null
     int32_t *keep = nullptr;
     int64_t keep_r = 0, t0 = 0, R0 = 0;
+    // tile width to start from (diagonals per CTA; 0: what the longest
+    // string could need).  Narrow tiles leave most of the SM's unified
+    // L1/shared memory to the L1, which holds the rows' string bytes.
+    int64_t smax_want = 0;
 };
 
 // What a tile launch left for one pair: its distance (st 0), or ST_WIDE,
@@ -156,7 +161,7 @@ struct ed_ctx {
     size_t held = 0;
     // pool
     DevBuf strA, strB, gf, ctl, gctl, slots, halo, pdesc, res, dump, hashA, hashB, scan, qx, qy, qo, bpairs,
-        border, bnext, bfront;
+        border, bnext, bfront, keep;
     unsigned long long *h_res = nullptr; // pinned result block
     size_t h_res_cap = 0;
     uint64_t hash_base = 0;
@@ -315,12 +320,13 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     });
     std::vector<int> npc(ncls, 0), ng(ncls, 0);
     std::vector<double> wc(ncls, 0.0);
-    std::vector<int64_t> nmc(ncls, 0);
+    std::vector<int64_t> nmc(ncls, 0), wantc(ncls, 0);
     for (int i = 0; i < np; i++) {
         const int c = cls_of(sizes[i]);
         npc[c]++;
         wc[c] += std::max(jobs[i].cost, 1.0);
         nmc[c] = std::max(nmc[c], std::max(jobs[i].n, jobs[i].m));
+        wantc[c] = std::max<int64_t>(wantc[c], jobs[i].smax_want > 0 ? jobs[i].smax_want : SMAX_LIMIT);
     }
     int used = 0;
     for (int c = ncls - 1; c >= 0; c--)
@@ -351,12 +357,14 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     kcap = std::max<int64_t>(kcap, h);
     // tile capacity: what the widest band of any class needs, at most SMAX_LIMIT
     // (a group also runs pairs of the classes below its own)
-    int64_t smax = std::max(h, s0), nm_below = 0;
+    int64_t smax = std::max(h, s0), nm_below = 0, want_below = 0;
     for (int c = 0; c < ncls; c++) {
         nm_below = std::max(nm_below, nmc[c]);
+        want_below = std::max(want_below, wantc[c]);
         if (ng[c] > 0)
             smax = std::max<int64_t>(
-                smax, std::min<int64_t>(SMAX_LIMIT, (2 * std::min(kcap, nm_below) + 1 + Gs[c] - 1) / Gs[c] + 1));
+                smax, std::min<int64_t>(std::min<int64_t>(SMAX_LIMIT, want_below),
+                                        (2 * std::min(kcap, nm_below) + 1 + Gs[c] - 1) / Gs[c] + 1));
     }
     LvArgs P{};
     int ngroups = 0;
@@ -466,7 +474,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
         const unsigned long long *R = ctx->h_res + (size_t)R_COUNT * q;
         TileOut &o = out[i];
         o.st = (uint32_t)R[R_STATUS];
-        if (o.st == ST_SUSPENDED) {
+        if (o.st == ST_SUSPENDED || (o.st == ST_WIDE && R[R_RESUME_T] > 0)) {
             o.rt = (int64_t)R[R_RESUME_T];
             o.rr = (int64_t)R[R_RESUME_R];
             // rounds t0 .. rt - 1 done in this launch
@@ -517,9 +525,18 @@ int run_tiles(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStream_t s, std
         for (size_t i = 0; i < cur.size(); i++) {
             if (o[i].st == 0) {
                 k[idx[i]] = o[i].k;
-            } else if (o[i].st == ST_WIDE && cur[i].G < ctx->grid) {
+            } else if (o[i].st == ST_WIDE &&
+                       (cur[i].G < ctx->grid || (cur[i].smax_want > 0 && cur[i].smax_want < SMAX_LIMIT))) {
+                // wider tiles first, then a larger group; from the saved
+                // round when the kernel left one in the pair's keep buffer
                 TileJob j = cur[i];
-                j.G = std::min(ctx->grid, 2 * std::max(1, j.G));
+                if (j.smax_want > 0 && j.smax_want < SMAX_LIMIT)
+                    j.smax_want = std::min<int64_t>(SMAX_LIMIT, 4 * j.smax_want);
+                else
+                    j.G = std::min(ctx->grid, 2 * std::max(1, j.G));
+                const bool resume = j.keep && o[i].rt > 0;
+                j.t0 = resume ? o[i].rt : 0;
+                j.R0 = resume ? o[i].rr : 0;
                 next.push_back(j);
                 nidx.push_back(idx[i]);
             } else {
@@ -543,6 +560,13 @@ int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64
 {
     int r;
     TileJob j{dA, dB, n, m, nullptr, nullptr, dump, dump_tmax, ctx->grid, 1.0};
+    // narrow tiles first (a large L1), saved and resumed on wider ones when
+    // the band outgrows them
+    j.smax_want = START_TILE;
+    j.keep_r = std::min<int64_t>(std::max(n, m), (int64_t)ctx->grid * SMAX_LIMIT);
+    if ((r = ensure(ctx, ctx->keep, sizeof(int32_t) * (size_t)(2 * j.keep_r + 5))) != ED_OK)
+        return r;
+    j.keep = (int32_t *)ctx->keep.p;
     if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
         CK(cudaEventRecord(ctx->ev2, s));
         if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
@@ -656,7 +680,8 @@ int ed_destroy(ed_ctx *ctx)
     DevBuf *bufs[] = {&ctx->strA,  &ctx->strB,   &ctx->gf,    &ctx->ctl,    &ctx->gctl,      &ctx->slots,
                       &ctx->halo,  &ctx->pdesc,  &ctx->res,   &ctx->dump,   &ctx->hashA,     &ctx->hashB,
                       &ctx->scan,  &ctx->qx,     &ctx->qy,    &ctx->qo,     &ctx->bpairs,    &ctx->border,
-                      &ctx->bnext, &ctx->bfront, &ctx->arena_buf, &ctx->s_pairs, &ctx->s_order, &ctx->s_next};
+                      &ctx->bnext, &ctx->bfront, &ctx->arena_buf, &ctx->s_pairs, &ctx->s_order, &ctx->s_next,
+                      &ctx->keep};
     for (DevBuf *b : bufs)
         release(ctx, *b);
     if (ctx->h_res)

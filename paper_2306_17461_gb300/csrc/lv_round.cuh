@@ -48,58 +48,79 @@ __device__ __forceinline__ int64_t start_row(const int32_t *prev, int64_t off, i
 // together so that their loads are in flight together.  Diagonals whose
 // slide is still open are listed; the list holds one entry per computed
 // diagonal at most, so it cannot fill.  Counts only diagonals of [a, b).
+//
+// Rows, diagonals and lengths are below 2^31 (strings are shorter than
+// 2^31 bytes), so the round works in 32-bit integers; the one quantity that
+// can exceed that, m - d (up to n + m), appears only in the clamp, which
+// takes n whenever d <= m - n.
 template <int DPT> // diagonals per thread per batch
 __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
 {
     RoundCount out = {0, 0};
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int64_t base = R.lo; base <= R.hi; base += (int64_t)nt * DPT) {
-        int64_t c[DPT];
+    const int32_t n = (int32_t)R.n, m = (int32_t)R.m, mn = (int32_t)(R.m - R.n);
+    const int32_t off = (int32_t)R.off, lo = (int32_t)R.lo, hi = (int32_t)R.hi;
+    const int32_t a = (int32_t)R.a, b = (int32_t)R.b;
+    const bool first = R.tau == 0;
+    const int32_t *prev = R.prev;
+    int32_t *cur = R.cur;
+    uint32_t slide = 0, mism = 0;
+    for (int32_t base = lo; base <= hi; base += nt * DPT) {
+        int32_t c[DPT];
         uint2 wa[DPT], wb[DPT];
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            c[u] = 0;
+            const int32_t d = base + u * nt + tid;
+            c[u] = -1;
             wa[u] = wb[u] = make_uint2(0u, 0u);
-            if (d <= R.hi) {
-                c[u] = start_row(R.prev, R.off, d, R.tau, R.n, R.m);
-                if (c[u] < 0 || c[u] + d < 0) {
+            if (d <= hi) {
+                int32_t cc = 0;
+                if (!first) {
+                    const int32_t x1 = prev[d - 1 - off];
+                    const int32_t x2 = prev[d - off] + 1;
+                    const int32_t x3 = prev[d + 1 - off] + 1;
+                    cc = min(max(x1, max(x2, x3)), d <= mn ? n : m - d);
+                }
+                if (cc < 0 || cc + d < 0) {
                     // a start row outside the grid: record it, never load it
                     if (atomicCAS(R.err, 0u, 6u) == 0u) {
                         R.diag[0] = 6;
                         R.diag[1] = blockIdx.x;
                         R.diag[2] = (unsigned long long)R.tau;
-                        R.diag[3] = (unsigned long long)d;
-                        R.diag[4] = (unsigned long long)c[u];
-                        R.diag[5] = ((unsigned long long)(uint32_t)R.prev[d - 1 - R.off] << 32) |
-                                    (uint32_t)R.prev[d + 1 - R.off];
+                        R.diag[3] = (unsigned long long)(int64_t)d;
+                        R.diag[4] = (unsigned long long)(int64_t)cc;
+                        R.diag[5] = ((unsigned long long)(uint32_t)prev[d - 1 - off] << 32) |
+                                    (uint32_t)prev[d + 1 - off];
                         R.diag[6] = (unsigned long long)R.off;
                     }
-                    c[u] = -1; // skipped below: no load at a bad row
-                } else if (min(R.n - c[u], R.m - c[u] - d) > 0) {
-                    word_load2(R.A, R.n, R.B, R.m, c[u], c[u] + d, wa[u], wb[u]);
+                } else {
+                    c[u] = cc;
+                    if (min(n - cc, m - cc - d) > 0)
+                        word_load2(R.A, n, R.B, m, cc, cc + d, wa[u], wb[u]);
                 }
             }
         }
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
-            const int64_t d = base + (int64_t)u * nt + tid;
-            if (d <= R.hi && c[u] >= 0) {
-                const int64_t cc = c[u];
-                const int64_t full = min(R.n - cc, R.m - cc - d);
-                const int64_t l = word_slide2(R.A, R.B, cc, cc + d, full, wa[u], wb[u]);
+            const int32_t d = base + u * nt + tid;
+            if (d <= hi && c[u] >= 0) {
+                const int32_t cc = c[u];
+                const int32_t full = min(n - cc, m - cc - d);
+                const int32_t l = (int32_t)word_slide2(R.A, R.B, cc, cc + d, full, wa[u], wb[u]);
                 if (l >= 0) {
-                    R.cur[d - R.off] = (int32_t)(cc + l);
-                    if (d >= R.a && d < R.b) {
-                        out.slide += l;
-                        out.mism += (l < full);
+                    cur[d - off] = cc + l;
+                    if (d >= a && d < b) {
+                        slide += (uint32_t)l;
+                        mism += (l < full);
                     }
                 } else {
-                    R.open[atomicAdd(R.n1, 1)] = (int32_t)d;
+                    R.open[atomicAdd(R.n1, 1)] = d;
                 }
             }
         }
     }
+    out.slide = slide;
+    out.mism = mism;
     return out;
 }
 

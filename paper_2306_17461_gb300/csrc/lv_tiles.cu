@@ -567,6 +567,86 @@ __device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S
     return SlideCounts{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens};
 }
 
+// What one block of rounds adds to the counters, and whether it found k.
+struct BlockOut {
+    unsigned long long slide, mism, hashq, coll, longs, opens, tm_round, tm_open;
+    int fin;
+};
+
+// Rounds t .. t+h-1 on the tile [a, b) and its shrinking halo trapezoid.
+__device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, const Pair Q, int32_t *dump,
+                                          int32_t dump_tmax, unsigned long long *res, GroupCtl *gc, int64_t t,
+                                          int h, int64_t a, int64_t b)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t n = Q.n, m = Q.m, target = m - n;
+    const int64_t off = a - h - 1; // smem index = d - off
+    Counters C;
+    bool fin = false;
+    for (int r = 0; r < h && !fin; r++) {
+        const uint64_t tr0 = clock64();
+        const int64_t tau = t + r;
+        const int64_t ra = a - h + 1 + r, rb = b + h - 1 - r; // computed range [ra, rb)
+        const int64_t blo = max(-tau, -n), bhi = min(tau, m);
+        int32_t *cur = frontier(S, tau);
+        // outside the band: minus infinity
+        for (int64_t d = ra + tid; d < rb; d += nt)
+            if (d < blo || d > bhi)
+                cur[d - off] = NEG;
+        RoundArgs RA;
+        RA.A = Q.A;
+        RA.B = Q.B;
+        RA.n = n;
+        RA.m = m;
+        RA.prev = frontier(S, tau - 1);
+        RA.cur = cur;
+        RA.off = off;
+        RA.lo = max(ra, blo);
+        RA.hi = min(rb - 1, bhi);
+        RA.tau = tau;
+        RA.a = a;
+        RA.b = b;
+        RA.n1 = S.n1;
+        RA.open = S.ld;
+        RA.err = &P.ctl->error;
+        RA.diag = P.ctl->diag;
+        const RoundCount rc = tile_round<2048 / CTA_THREADS>(RA);
+        C.slide += rc.slide;
+        C.mism += rc.mism;
+        __syncthreads();
+        const uint64_t tr1 = clock64();
+        C.tm[0] += tr1 - tr0;
+        const int n1 = *S.n1;
+        if (n1 > 0) {
+            const SlideCounts oc = open_slides(P, S, Q, frontier(S, tau - 1), cur, off, tau, a, b, n1);
+            C.slide += oc.slide;
+            C.mism += oc.mism;
+            C.hashq += oc.hashq;
+            C.coll += oc.coll;
+            C.longs += oc.longs;
+            C.opens += oc.opens;
+            if (tid == 0)
+                *S.n1 = 0;
+            C.tm[1] += clock64() - tr1;
+        }
+        // termination: the tile owning the target diagonal reports k
+        if (target >= a && target < b && target >= blo && target <= bhi && cur[target - off] == n) {
+            fin = true;
+            if (tid == 0) {
+                atomicMin(&gc->done_k, (unsigned long long)tau);
+                res[R_K] = (unsigned long long)tau;
+            }
+        }
+        if (dump && tau <= dump_tmax) {
+            const int64_t TT = dump_tmax;
+            for (int64_t d = max(a, -TT) + tid; d < min(b, TT + 1); d += nt)
+                dump[tau * (2 * TT + 1) + d + TT] = cur[d - off];
+        }
+        __syncthreads();
+    }
+    return BlockOut{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens, C.tm[0], C.tm[1], fin ? 1 : 0};
+}
+
 // Whether a CTA that is about to compute round t leaves the pair.  Once k
 // is known every CTA leaves at once, except with a frontier dump: a CTA may
 // lag its neighbours by a few blocks, so it first computes every round up
@@ -640,6 +720,10 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
     Tile T = partition(Q, R, G, gi, c0, h);
     if (T.S > P.smax || (D.keep && R > D.keep_r)) {
         pair_stop(D, gc, ST_WIDE);
+        if (tid == 0 && gi == 0 && t > 0) { // the saved state is still good
+            D.res[R_RESUME_T] = (unsigned long long)t;
+            D.res[R_RESUME_R] = (unsigned long long)R;
+        }
         return true;
     }
     for (int i = tid; i < P.smax + 2 * HMAX + 2; i += nt) {
@@ -719,6 +803,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             // (a sync point of a time-sliced pair re-tiles at the same radius)
             const uint64_t te0 = clock64();
             int64_t Rn = R;
+            bool wide = false; // the band outgrew the tiles: save it for wider ones
             if (grow) {
                 Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
                 if (t + h - 1 > Rn && Rn < nm) {
@@ -730,8 +815,15 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 if (D.keep)
                     Rn = min(Rn, D.keep_r);
                 if (t + h - 1 > Rn && Rn < nm) {
-                    pair_stop(D, gc, ST_WIDE);
-                    return true;
+                    if (!D.keep) {
+                        pair_stop(D, gc, ST_WIDE);
+                        return true;
+                    }
+                    // every CTA of the group takes this decision at the same
+                    // round: the band of round t - 1 is saved below as for a
+                    // time slice, and the host resumes the pair on wider tiles
+                    wide = true;
+                    Rn = R;
                 }
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
@@ -742,7 +834,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             }
             if (leader) {
                 // the leader alone decides whether the launch leaves the pair here
-                gc->susp[(epoch + 1) & 1] = (can_suspend && gtimer() >= deadline) ? 1u : 0u;
+                gc->susp[(epoch + 1) & 1] = (wide || (can_suspend && gtimer() >= deadline)) ? 1u : 0u;
                 gc->epoch_t = (uint32_t)t;
                 __threadfence();
                 st_release(&gc->epoch_req, epoch + 1);
@@ -760,7 +852,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 for (int64_t d = plo + (int64_t)gi * nt + tid; d <= phi; d += (int64_t)G * nt)
                     D.keep[d + D.keep_r + 2] = ld_cg(buf + d + kc + 2);
                 if (leader) {
-                    D.res[R_STATUS] = ST_SUSPENDED;
+                    D.res[R_STATUS] = wide ? ST_WIDE : ST_SUSPENDED;
                     D.res[R_RESUME_T] = (unsigned long long)t;
                     D.res[R_RESUME_R] = (unsigned long long)Rn;
                 }
@@ -786,68 +878,16 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         }
         // ---------------------------------------------- h rounds
         const int64_t a = T.a, b = T.b, off = a - h - 1; // smem index = d - off
-        bool fin = false;
-        for (int r = 0; r < h && !fin; r++) {
-            const uint64_t tr0 = clock64();
-            const int64_t tau = t + r;
-            const int64_t ra = a - h + 1 + r, rb = b + h - 1 - r; // computed range [ra, rb)
-            const int64_t blo = max(-tau, -n), bhi = min(tau, m);
-            int32_t *cur = frontier(S, tau);
-            // outside the band: minus infinity
-            for (int64_t d = ra + tid; d < rb; d += nt)
-                if (d < blo || d > bhi)
-                    cur[d - off] = NEG;
-            RoundArgs RA;
-            RA.A = Q.A;
-            RA.B = Q.B;
-            RA.n = n;
-            RA.m = m;
-            RA.prev = frontier(S, tau - 1);
-            RA.cur = cur;
-            RA.off = off;
-            RA.lo = max(ra, blo);
-            RA.hi = min(rb - 1, bhi);
-            RA.tau = tau;
-            RA.a = a;
-            RA.b = b;
-            RA.n1 = S.n1;
-            RA.open = S.ld;
-            RA.err = &P.ctl->error;
-            RA.diag = P.ctl->diag;
-            const RoundCount rc = tile_round<2048 / CTA_THREADS>(RA);
-            C.slide += rc.slide;
-            C.mism += rc.mism;
-            __syncthreads();
-            const uint64_t tr1 = clock64();
-            C.tm[0] += tr1 - tr0;
-            const int n1 = *S.n1;
-            if (n1 > 0) {
-                const SlideCounts oc = open_slides(P, S, Q, frontier(S, tau - 1), cur, off, tau, a, b, n1);
-                C.slide += oc.slide;
-                C.mism += oc.mism;
-                C.hashq += oc.hashq;
-                C.coll += oc.coll;
-                C.longs += oc.longs;
-                C.opens += oc.opens;
-                if (tid == 0)
-                    *S.n1 = 0;
-                C.tm[1] += clock64() - tr1;
-            }
-            // termination: the tile owning the target diagonal reports k
-            if (target >= a && target < b && target >= blo && target <= bhi && cur[target - off] == n) {
-                fin = true;
-                if (tid == 0) {
-                    atomicMin(&gc->done_k, (unsigned long long)tau);
-                    D.res[R_K] = (unsigned long long)tau;
-                }
-            }
-            if (D.dump && tau <= D.dump_tmax) {
-                const int64_t TT = D.dump_tmax;
-                for (int64_t d = max(a, -TT) + tid; d < min(b, TT + 1); d += nt)
-                    D.dump[tau * (2 * TT + 1) + d + TT] = cur[d - off];
-            }
-            __syncthreads();
-        }
+        const BlockOut bo = run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
+        C.slide += bo.slide;
+        C.mism += bo.mism;
+        C.hashq += bo.hashq;
+        C.coll += bo.coll;
+        C.longs += bo.longs;
+        C.opens += bo.opens;
+        C.tm[0] += bo.tm_round;
+        C.tm[1] += bo.tm_open;
+        const bool fin = bo.fin != 0;
         if (fin)
             return true;
         t += h;

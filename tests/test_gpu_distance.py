@@ -162,3 +162,22 @@ def test_round_cap_is_reported():
         assert e.value.code == ed.ED_ELIMIT
         q = W.make_pair(96, 20_000, 20, sigma=4)
         assert ed.ed_distance_dev(c.h, dev(q.A), dev(q.B)) <= 20
+
+
+def test_band_outgrows_tiles_and_resumes(orc):
+    """A single pair starts on narrow tiles (2048 diagonals per CTA).  When
+    its band outgrows them, the group saves the band frontier and the host
+    resumes from that round on tiles four times wider.  On one CTA, a pair
+    at k ~ 6000 resumes twice (2048 -> 8192 -> 16384); the distance is the
+    oracle's and no round is recomputed."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    p = W.make_pair(120, 100_000, 6000, sigma=4)
+    want = orc.lv(p.A, p.B)
+    assert want > 4096  # the band (2k + 1 diagonals) passes 8192
+    with ed.Context(device=0, grid_ctas=1) as c:
+        assert ed.ed_distance_dev(c.h, dev(p.A), dev(p.B)) == want
+        st = c.stats()
+        assert st["kernel_launches"] == 3
+        # every round counted once: a resumed launch starts where the last stopped
+        assert st["extensions"] == orc.lv(p.A, p.B, with_stats=True)[2]
