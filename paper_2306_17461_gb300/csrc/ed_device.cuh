@@ -259,6 +259,10 @@ static __device__ __noinline__ int64_t slide_more(const uint8_t *A, int64_t n, c
     return l;
 }
 
+// Slides at least this long are followed by a prefetch of what follows
+// them (shorter ones are chance matches off the alignment path).
+constexpr int64_t PREFETCH_MIN = 256;
+
 // Asks L2 for the 4 KiB of each string that follow rows x (of A) and y (of
 // B), one 128-byte line per lane of the calling warp: a diagonal that just
 // ended a long slide starts its next round there.  Only addresses inside

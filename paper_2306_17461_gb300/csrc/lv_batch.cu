@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
                     const int64_t lim = c + min(n - c, m - c - d);
                     bool open;
                     const int64_t l = warp_slide(A, n, B, m, c, d, lim - c, Bg.t2_cap, &open);
-                    if (!open)
+                    if (!open && l >= PREFETCH_MIN)
                         prefetch_next(A, n, B, m, c + l, c + l + d);
                     if (lane == 0) {
                         if (!open) {

@@ -530,7 +530,7 @@ __device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S
             lim = __shfl_sync(0xffffffffu, lim, 0);
             bool open;
             const int64_t l = slide_warp(Q.A, Q.n, Q.B, Q.m, c, c + d, 0, lim - c, P.t2_cap, &open);
-            if (!open)
+            if (!open && l >= PREFETCH_MIN) // a long slide: the next round starts past it
                 prefetch_next(Q.A, Q.n, Q.B, Q.m, c + l, c + l + d);
             if (lane == 0) {
                 if (!open) {
