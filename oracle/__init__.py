@@ -17,6 +17,9 @@ What it computes, with the passage each function follows:
 * ``lcp``           -- LCP(A, B, x, y) of Sec. 2, one character at a time.
 * ``prefix_hash``   -- T[x] = h(X[1..x]) of Sec. 2 / Sec. 3.2, mod 2^61-1.
 * ``hash_lcp``      -- the doubling-then-binary search LCP of Sec. 3.2.
+* ``prefix_hash_blocked``, ``get_hash_blocked``, ``hash_lcp_blocked`` --
+  the blocked table of Sec. 3.3 (Alg. 2: block prefixes only, GetHash
+  extends them by the characters after the last whole block).
 * ``many``          -- DP or Algorithm 1 over many pairs (host threads).
 
 The arithmetic lives in ``oracle.c`` (plain C, int64, exact 128-bit
@@ -79,6 +82,12 @@ def _load():
     lib.orc_powmod.argtypes = [u64, i64]
     lib.orc_hash_lcp.restype = i64
     lib.orc_hash_lcp.argtypes = [vp, i64, vp, i64, u64, i64, i64]
+    lib.orc_prefix_hash_blocked.restype = ci
+    lib.orc_prefix_hash_blocked.argtypes = [vp, i64, i64, u64, vp]
+    lib.orc_get_hash_blocked.restype = u64
+    lib.orc_get_hash_blocked.argtypes = [vp, vp, i64, u64, i64]
+    lib.orc_hash_lcp_blocked.restype = i64
+    lib.orc_hash_lcp_blocked.argtypes = [vp, i64, vp, vp, i64, vp, i64, u64, i64, i64]
     lib.orc_num_threads.restype = ci
     lib.orc_num_threads.argtypes = []
     _lib = lib
@@ -190,3 +199,24 @@ def powmod(base: int, e: int) -> int:
 def hash_lcp(TA: np.ndarray, n: int, TB: np.ndarray, m: int, base: int, x: int, y: int) -> int:
     return int(_load().orc_hash_lcp(TA.ctypes.data_as(ctypes.c_void_p), n,
                                     TB.ctypes.data_as(ctypes.c_void_p), m, base, x, y))
+
+
+def prefix_hash_blocked(X, b: int, base: int) -> np.ndarray:
+    """TB[j] = h(X[0..j*b)) for j = 0..len(X)//b (Sec. 3.3, Alg. 2 Build)."""
+    x = _u8(X)
+    TB = np.zeros(x.size // b + 1, dtype=np.uint64)
+    _load().orc_prefix_hash_blocked(_ptr(x), x.size, b, base, TB.ctypes.data_as(ctypes.c_void_p))
+    return TB
+
+
+def get_hash_blocked(X, TB: np.ndarray, b: int, base: int, i: int) -> int:
+    """h(X[0..i)) from the blocked table (Alg. 2 GetHash)."""
+    x = _u8(X)
+    return int(_load().orc_get_hash_blocked(_ptr(x), TB.ctypes.data_as(ctypes.c_void_p), b, base, i))
+
+
+def hash_lcp_blocked(A, TA: np.ndarray, B, TB: np.ndarray, b: int, base: int, x: int, y: int) -> int:
+    """The LCP search of Sec. 3.2 on blocked tables (Alg. 2 LongestPrefix)."""
+    a, bb = _u8(A), _u8(B)
+    return int(_load().orc_hash_lcp_blocked(_ptr(a), a.size, TA.ctypes.data_as(ctypes.c_void_p), _ptr(bb), bb.size,
+                                            TB.ctypes.data_as(ctypes.c_void_p), b, base, x, y))

@@ -377,20 +377,73 @@ uint64_t orc_powmod(uint64_t base, int64_t e)
     return r;
 }
 
-/* LCP by hashes, Sec. 3.2: compare chunks of length 1, 2, 4, ... until the
- * first unequal one, then binary-search the length inside the last
- * bracket.  Returns the largest l <= min(n-x, m-y) whose length-l hashes
- * agree (reading of the garbled Algorithm 2 search; no confirmation here:
- * the oracle reports what the hashes say).                             */
-int64_t orc_hash_lcp(const uint64_t *TA, int64_t n, const uint64_t *TB,
-                     int64_t m, uint64_t base, int64_t x, int64_t y)
+/* Blocked prefix-hash table of Sec. 3.3 (Alg. 2, Build): the prefix hashes
+ * of whole blocks only, TB[j] = h(X[0..j*b)) for j = 0 .. floor(len/b).
+ * Built the paper's way: every block hashed on its own, then a scan that
+ * concatenates them (Sec. 2: h(S1 S2) = h(S1) * p^|S2| + h(S2), |S2| = b). */
+int orc_prefix_hash_blocked(const uint8_t *X, int64_t len, int64_t b,
+                            uint64_t base, uint64_t *TB)
+{
+    const int64_t w = len / b;
+    const uint64_t pb = orc_powmod(base, b);
+    TB[0] = 0;
+    for (int64_t j = 1; j <= w; j++) {
+        uint64_t hb = 0; /* h(X[(j-1)b .. jb)) */
+        for (int64_t i = (j - 1) * b; i < j * b; i++)
+            hb = (mulmod_q(hb, base) + (uint64_t)X[i] + 1) % ORC_Q;
+        TB[j] = (mulmod_q(TB[j - 1], pb) + hb) % ORC_Q;
+    }
+    return 0;
+}
+
+/* GetHash of Alg. 2: h(X[0..i)) from the blocked table, the prefix of the
+ * last whole block at or before i (r = floor(i/b); the printed formula
+ * for r is garbled) extended by the i - r*b < b characters after it. */
+uint64_t orc_get_hash_blocked(const uint8_t *X, const uint64_t *TB, int64_t b,
+                              uint64_t base, int64_t i)
+{
+    const int64_t r = i / b;
+    uint64_t h = TB[r] % ORC_Q;
+    for (int64_t j = r * b; j < i; j++)
+        h = (mulmod_q(h, base) + (uint64_t)X[j] + 1) % ORC_Q;
+    return h;
+}
+
+/* A prefix-hash table as the LCP search sees it: full (b = 1: T[i] is
+ * h(X[0..i)) itself) or blocked (GetHash). */
+struct orc_htab {
+    const uint64_t *T;
+    const uint8_t *X;
+    int64_t b;
+};
+
+static uint64_t htab_prefix(const struct orc_htab *t, uint64_t base, int64_t i)
+{
+    return t->b == 1 ? t->T[i] % ORC_Q : orc_get_hash_blocked(t->X, t->T, t->b, base, i);
+}
+
+/* h(X[l..l+len)) = h(X[0..l+len)) - p^len * h(X[0..l)) (Sec. 2). */
+static uint64_t htab_range(const struct orc_htab *t, uint64_t base, int64_t l,
+                           int64_t len)
+{
+    const uint64_t a = htab_prefix(t, base, l + len);
+    const uint64_t c = mulmod_q(htab_prefix(t, base, l), orc_powmod(base, len));
+    return (a + ORC_Q - c) % ORC_Q;
+}
+
+/* LCP by hashes, Sec. 3.2 and Alg. 2's LongestPrefix: compare chunks of
+ * length 1, 2, 4, ... until the first unequal one, then binary-search the
+ * length inside the last bracket.  Returns the largest l <= min(n-x, m-y)
+ * whose length-l hashes agree (reading of the garbled search; no
+ * confirmation here: the oracle reports what the hashes say).            */
+static int64_t htab_lcp(const struct orc_htab *ta, int64_t n,
+                        const struct orc_htab *tb, int64_t m, uint64_t base,
+                        int64_t x, int64_t y)
 {
     int64_t lim = (n - x) < (m - y) ? (n - x) : (m - y);
     if (lim <= 0)
         return 0;
-#define ORC_EQ(L)                                                            \
-    (orc_range_hash(TA, x, (L), orc_powmod(base, (L))) ==                    \
-     orc_range_hash(TB, y, (L), orc_powmod(base, (L))))
+#define ORC_EQ(L) (htab_range(ta, base, x, (L)) == htab_range(tb, base, y, (L)))
     if (!ORC_EQ(1))
         return 0;
     int64_t good = 1; /* longest length known equal */
@@ -419,6 +472,22 @@ int64_t orc_hash_lcp(const uint64_t *TA, int64_t n, const uint64_t *TB,
     }
 #undef ORC_EQ
     return good;
+}
+
+int64_t orc_hash_lcp(const uint64_t *TA, int64_t n, const uint64_t *TB,
+                     int64_t m, uint64_t base, int64_t x, int64_t y)
+{
+    const struct orc_htab ta = {TA, 0, 1}, tb = {TB, 0, 1};
+    return htab_lcp(&ta, n, &tb, m, base, x, y);
+}
+
+/* The same search with blocked tables (Alg. 2): every hash from GetHash. */
+int64_t orc_hash_lcp_blocked(const uint8_t *A, int64_t n, const uint64_t *TA,
+                             const uint8_t *B, int64_t m, const uint64_t *TB,
+                             int64_t b, uint64_t base, int64_t x, int64_t y)
+{
+    const struct orc_htab ta = {TA, A, b}, tb = {TB, B, b};
+    return htab_lcp(&ta, n, &tb, m, base, x, y);
 }
 
 int orc_num_threads(void)

@@ -83,3 +83,79 @@ def test_hash_lcp_equals_direct_lcp(orc):
             x = int(rng.integers(0, 3001))
             y = x if rng.random() < 0.6 else int(rng.integers(0, 3001))
             assert orc.hash_lcp(TA, A.size, TB, B.size, base, x, y) == orc.lcp(A, B, x, y)
+
+
+# ---------------------------------------------------------------- blocked
+# Sec. 3.3 / Alg. 2: the table keeps the prefixes of whole blocks only, and
+# GetHash extends the last one by the characters after it.
+
+@pytest.mark.parametrize("b", [1, 2, 7, 32, 64, 500])
+def test_blocked_table_definition(orc, b):
+    """TB[j] is the defining sum over X[0..j*b), in Python integers (the
+    oracle builds it differently: block hashes joined by a scan)."""
+    base = 1000003
+    rng = np.random.default_rng(b)
+    X = rng.integers(0, 256, 333, dtype=np.uint8)
+    TB = orc.prefix_hash_blocked(X, b, base)
+    assert TB.size == X.size // b + 1 and TB[0] == 0
+    xb = X.tobytes()
+    for j in range(TB.size):
+        assert int(TB[j]) == _sum_hash(xb[:j * b], base), (b, j)
+
+
+@pytest.mark.parametrize("b", [1, 3, 32])
+def test_blocked_table_is_the_full_table_every_b(orc, b):
+    base = 257
+    rng = np.random.default_rng(5 + b)
+    X = rng.integers(0, 4, 5000, dtype=np.uint8)
+    T = orc.prefix_hash(X, base)
+    TB = orc.prefix_hash_blocked(X, b, base)
+    assert np.array_equal(TB, T[::b][:TB.size])
+
+
+@pytest.mark.parametrize("b", [1, 5, 32])
+def test_get_hash_blocked_every_prefix(orc, b):
+    """GetHash(i) = h(X[0..i)) for every i, block boundaries and the string
+    end included (against the defining sum on a short string, against the
+    full table on a longer one)."""
+    base = (1 << 40) + 15
+    rng = np.random.default_rng(11 * b)
+    X = rng.integers(0, 256, 97, dtype=np.uint8)
+    TB = orc.prefix_hash_blocked(X, b, base)
+    xb = X.tobytes()
+    for i in range(X.size + 1):
+        assert orc.get_hash_blocked(X, TB, b, base, i) == _sum_hash(xb[:i], base), (b, i)
+    Y = rng.integers(0, 3, 4000, dtype=np.uint8)
+    T = orc.prefix_hash(Y, base)
+    TBy = orc.prefix_hash_blocked(Y, b, base)
+    for i in rng.integers(0, Y.size + 1, 300):
+        assert orc.get_hash_blocked(Y, TBy, b, base, int(i)) == int(T[int(i)])
+
+
+def test_blocked_string_shorter_than_a_block(orc):
+    X = np.arange(10, dtype=np.uint8)
+    TB = orc.prefix_hash_blocked(X, 32, 257)
+    assert TB.tolist() == [0]
+    assert orc.get_hash_blocked(X, TB, 32, 257, 0) == 0
+    assert orc.get_hash_blocked(X, TB, 32, 257, 10) == _sum_hash(X.tobytes(), 257)
+
+
+@pytest.mark.parametrize("b", [1, 32])
+def test_blocked_hash_lcp_equals_direct_lcp(orc, b):
+    """The search on blocked tables finds the character LCP (no collision
+    on these inputs), including LCPs that cross many blocks and end at a
+    string end."""
+    base = 1000003
+    rng = np.random.default_rng(40 + b)
+    n = 3000
+    A = rng.integers(0, 2, n, dtype=np.uint8)
+    B = A.copy()
+    flips = rng.choice(n, 40, replace=False)
+    B[flips] ^= 1
+    TA = orc.prefix_hash_blocked(A, b, base)
+    TB = orc.prefix_hash_blocked(B, b, base)
+    for _ in range(300):
+        x = int(rng.integers(0, n + 1))
+        y = min(n, max(0, x + int(rng.integers(-3, 4))))
+        want = orc.lcp(A, B, x, y)
+        assert orc.hash_lcp_blocked(A, TA, B, TB, b, base, x, y) == want, (x, y)
