@@ -208,7 +208,7 @@ def run_single(args, D: Dist):
     torch.cuda.set_device(D.local)
     dev = torch.device("cuda", D.local)
     pairs, desc = make_workload(args.workload, args)
-    lcp_mode = {"direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH}[args.lcp]
+    lcp_mode = {"direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH, "bhash": ed.ED_LCP_BHASH}[args.lcp]
     ctx = ed.Context(device=D.local, lcp_mode=lcp_mode)
     dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
     dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
@@ -249,10 +249,12 @@ def run_single(args, D: Dist):
                                "ms": [], "ext": st["extensions"], "compared_bytes": st["compared_bytes"],
                                "long_slides": st["long_slides"], "open_slides": st["open_slides"],
                                "wide_rounds": st["wide_rounds"],
-                               "phase_ms": [round(x, 3) for x in st["phase_ms"]]})
+                               "phase_ms": [round(x, 3) for x in st["phase_ms"]], "build_ms": []})
         d["ms"].append(st["kernel_ms"])
+        d["build_ms"].append(st["build_ms"])
     for d in per.values():
         d["ms"] = round(statistics.median(d["ms"]), 4)
+        d["build_ms"] = round(statistics.median(d["build_ms"]), 4)
         d["ext_per_s"] = d["ext"] / (d["ms"] / 1e3) if d["ms"] else None
     # e2e: host buffers through ed_distance (H2D inside the timed region)
     hA = [torch.from_numpy(p.A).pin_memory() for p in pairs]
@@ -520,7 +522,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="mid", choices=["mid", "small", "large", "batch", "serve"])
-    ap.add_argument("--lcp", default="direct", choices=["direct", "hash"])
+    ap.add_argument("--lcp", default="direct", choices=["direct", "hash", "bhash"])
     ap.add_argument("--ks", default="10,1000,100000")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--npairs", type=int, default=4096)

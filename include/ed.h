@@ -50,7 +50,10 @@ typedef enum {
 typedef enum {
     ED_LCP_AUTO = 0,   /* autotuner picks direct or hash per call */
     ED_LCP_DIRECT = 1, /* 16-byte direct comparison (Sec. 5.1 fast path) */
-    ED_LCP_HASH = 2    /* prefix-hash doubling search, confirmed directly */
+    ED_LCP_HASH = 2,   /* prefix-hash doubling search, confirmed directly */
+    ED_LCP_BHASH = 3   /* the same search on blocked prefix tables (Sec. 3.3,
+                          Alg. 2: hashes of whole blocks only, hash_block
+                          characters each), confirmed directly */
 } ed_lcp_mode;
 
 typedef struct {
@@ -67,6 +70,8 @@ typedef struct {
                                  0 = 16 */
     int64_t max_rounds;       /* frontier capacity in rounds; 0 = the larger
                                  string length (at most 2^28) */
+    int hash_block;           /* block size b of ED_LCP_BHASH (1..4096);
+                                 0 = 32 */
 } ed_config;
 
 typedef struct {
@@ -159,8 +164,11 @@ int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed,
 /* LCP(A, B, x[i], y[i]) of Sec. 2 for q queries; A, B device pointers;
  * x, y, out host arrays.  method: 0 = per-thread 16-byte compare, 1 = one
  * warp per query (ballot / first-set-bit), 2 = whole-grid search,
- * 3 = hash search (needs ed_prefix_hash tables TA, TB as device pointers of
- * n+1 and m+1 entries; confirmed directly).  Synchronous. */
+ * 3 = hash search alone (needs ed_prefix_hash tables TA, TB as device
+ * pointers of n+1 and m+1 entries; may differ from the LCP on a hash
+ * collision), 4 = hash search confirmed directly (exact), 5 and 6 = 3 and 4
+ * on blocked tables (ed_prefix_hash_blocked_dev with the context's
+ * hash_block b: n/b+1 and m/b+1 entries).  Synchronous. */
 int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
                size_t m, const int64_t *x, const int64_t *y, size_t q,
                int method, const uint64_t *TA, const uint64_t *TB,
@@ -171,6 +179,14 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
  * pointers; T has len + 1 uint64 entries.  One single-pass scan launch. */
 int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T,
                        void *stream);
+
+/* The blocked prefix table of Sec. 3.3 (Alg. 2): T[j] = h(X[0..j*b)) for
+ * j = 0..len/b, the entries of ed_prefix_hash_dev's table at multiples of
+ * b (1 <= b <= 2^20).  X and T are device pointers; T has len/b + 1 uint64
+ * entries.  One scan launch that writes only the block prefixes.
+ * Synchronous on `stream`. */
+int ed_prefix_hash_blocked_dev(ed_ctx *ctx, const uint8_t *X, size_t len, size_t b, uint64_t *T,
+                               void *stream);
 
 /* The hash base p used by the context (derived from hash_seed). */
 uint64_t ed_hash_base(ed_ctx *ctx);

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libedgb300.so")
 
 ED_OK, ED_EAGAIN = 0, 1
 ED_EINVAL, ED_ENOMEM, ED_ECUDA, ED_ETIMEOUT, ED_EBUSY, ED_ENOTFOUND, ED_ELIMIT = -1, -2, -3, -4, -5, -6, -7
-ED_LCP_AUTO, ED_LCP_DIRECT, ED_LCP_HASH = 0, 1, 2
+ED_LCP_AUTO, ED_LCP_DIRECT, ED_LCP_HASH, ED_LCP_BHASH = 0, 1, 2, 3
 NEG32 = -1061109568  # 0xC0C0C0C0: "minus infinity" in frontier dumps
 
 
@@ -42,6 +42,7 @@ class ed_config(ctypes.Structure):
         ("tile_width", ctypes.c_int),
         ("block_rounds", ctypes.c_int),
         ("max_rounds", ctypes.c_int64),
+        ("hash_block", ctypes.c_int),
     ]
 
 
@@ -83,6 +84,7 @@ _SIGS = {
     "ed_serve_counters": (_I, [_P, _P, _P, _P, _P, _P]),
     "ed_lcp_dev": (_I, [_P, _P, _S, _P, _S, _P, _P, _S, _I, _P, _P, _P, _P]),
     "ed_prefix_hash_dev": (_I, [_P, _P, _S, _P, _P]),
+    "ed_prefix_hash_blocked_dev": (_I, [_P, _P, _S, _S, _P, _P]),
     "ed_hash_base": (_U64, [_P]),
     "ed_frontiers_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _P, _P]),
     "ed_prefix_hash_noalloc": (_I, [_P, _S, _U64, _P, _P]),
@@ -288,6 +290,17 @@ def ed_prefix_hash_dev(ctx, X, stream=None):
     T = torch.empty(n + 1, dtype=torch.int64, device=X.device)
     _check(ctx, load().ed_prefix_hash_dev(ctx, px, n, T.data_ptr(), _stream_ptr(stream)),
            "ed_prefix_hash_dev")
+    return T
+
+
+def ed_prefix_hash_blocked_dev(ctx, X, b: int, stream=None):
+    """T[0..len//b] (block prefixes of Sec. 3.3) as an int64 CUDA tensor."""
+    import torch
+
+    px, n = _dev_buf(X)
+    T = torch.empty(n // b + 1, dtype=torch.int64, device=X.device)
+    _check(ctx, load().ed_prefix_hash_blocked_dev(ctx, px, n, b, T.data_ptr(), _stream_ptr(stream)),
+           "ed_prefix_hash_blocked_dev")
     return T
 
 

@@ -263,20 +263,30 @@ uint64_t count_extensions(int64_t n, int64_t m, int64_t k)
 
 bool bad_len(size_t n) { return n > (size_t)MAX_LEN; }
 
+bool hash_mode(const ed_ctx *ctx) { return ctx->cfg.lcp_mode == ED_LCP_HASH || ctx->cfg.lcp_mode == ED_LCP_BHASH; }
+
+// Stride of the context's prefix tables: 1 (full, Sec. 3.2) or the block
+// size of Sec. 3.3 (blocked, Alg. 2).
+int64_t hash_stride(const ed_ctx *ctx)
+{
+    return ctx->cfg.lcp_mode == ED_LCP_BHASH ? (int64_t)ctx->cfg.hash_block : 1;
+}
+
 int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
                     cudaStream_t s)
 {
     int r;
-    if ((r = ensure(ctx, ctx->hashA, sizeof(uint64_t) * (n + 1))) != ED_OK)
+    const int64_t b = hash_stride(ctx);
+    if ((r = ensure(ctx, ctx->hashA, sizeof(uint64_t) * (n / b + 1))) != ED_OK)
         return r;
-    if ((r = ensure(ctx, ctx->hashB, sizeof(uint64_t) * (m + 1))) != ED_OK)
+    if ((r = ensure(ctx, ctx->hashB, sizeof(uint64_t) * (m / b + 1))) != ED_OK)
         return r;
     const size_t sb = std::max(prefix_hash_state_bytes(n), prefix_hash_state_bytes(m));
     if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
         return r;
-    CK(launch_prefix_hash(dA, n, ctx->hash_base, (uint64_t *)ctx->hashA.p, ctx->scan.p,
+    CK(launch_prefix_hash(dA, n, ctx->hash_base, (uint64_t *)ctx->hashA.p, b, ctx->scan.p,
                           prefix_hash_state_bytes(n), s));
-    CK(launch_prefix_hash(dB, m, ctx->hash_base, (uint64_t *)ctx->hashB.p, ctx->scan.p,
+    CK(launch_prefix_hash(dB, m, ctx->hash_base, (uint64_t *)ctx->hashB.p, b, ctx->scan.p,
                           prefix_hash_state_bytes(m), s));
     ctx->last.kernel_launches += 2;
     return ED_OK;
@@ -436,6 +446,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.s0 = s0;
     P.t2_cap = 4096;
     P.use_hash = jobs[0].TA != nullptr;
+    P.hash_b = (int32_t)hash_stride(ctx);
     std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
     P.spin_ns = ctx->cfg.spin_limit_ns;
     P.idle_ns = ctx->cfg.spin_limit_ns * 60;
@@ -567,7 +578,7 @@ int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64
     if ((r = ensure(ctx, ctx->keep, sizeof(int32_t) * (size_t)(2 * j.keep_r + 5))) != ED_OK)
         return r;
     j.keep = (int32_t *)ctx->keep.p;
-    if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
+    if (hash_mode(ctx)) {
         CK(cudaEventRecord(ctx->ev2, s));
         if ((r = run_hash_tables(ctx, dA, n, dB, m, s)) != ED_OK)
             return r;
@@ -577,7 +588,7 @@ int run_pair(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64
     std::vector<uint64_t> k;
     if ((r = run_tiles(ctx, {j}, s, k)) != ED_OK)
         return r;
-    if (ctx->cfg.lcp_mode == ED_LCP_HASH) {
+    if (hash_mode(ctx)) {
         float bms = 0.f;
         cudaEventElapsedTime(&bms, ctx->ev2, ctx->ev0);
         ctx->last.build_ms += bms;
@@ -637,8 +648,10 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
         c->cfg.spin_limit_ns = 2000000000ull;
     if (c->cfg.max_inflight <= 0)
         c->cfg.max_inflight = 1024;
-    if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 2 || c->cfg.tile_width < 0 || c->cfg.block_rounds < 0 ||
-        c->cfg.tile_width > SMAX_LIMIT)
+    if (c->cfg.hash_block == 0)
+        c->cfg.hash_block = 32;
+    if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 3 || c->cfg.tile_width < 0 || c->cfg.block_rounds < 0 ||
+        c->cfg.tile_width > SMAX_LIMIT || c->cfg.hash_block < 1 || c->cfg.hash_block > 4096)
         return ED_EINVAL;
     int dev = c->cfg.device;
     if (dev < 0)
@@ -777,7 +790,23 @@ int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T, v
     if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
         return r;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, ctx->scan.p, sb, s));
+    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, 1, ctx->scan.p, sb, s));
+    CK(cudaStreamSynchronize(s));
+    return ED_OK;
+}
+
+int ed_prefix_hash_blocked_dev(ed_ctx *ctx, const uint8_t *X, size_t len, size_t b, uint64_t *T, void *stream)
+{
+    if (!ctx || !T || (len && !X) || bad_len(len) || b < 1 || b > (size_t)1 << 20)
+        return ED_EINVAL;
+    std::lock_guard<std::mutex> g(ctx->api_mu);
+    CK(cudaSetDevice(ctx->device));
+    int r;
+    const size_t sb = prefix_hash_state_bytes((int64_t)len);
+    if ((r = ensure(ctx, ctx->scan, sb)) != ED_OK)
+        return r;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, (int64_t)b, ctx->scan.p, sb, s));
     CK(cudaStreamSynchronize(s));
     return ED_OK;
 }
@@ -786,9 +815,9 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
                const int64_t *y, size_t q, int method, const uint64_t *TA, const uint64_t *TB, int64_t *out,
                void *stream)
 {
-    if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 4 || bad_len(n) || bad_len(m))
+    if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 6 || bad_len(n) || bad_len(m))
         return ED_EINVAL;
-    if ((method == 3 || method == 4) && (!TA || !TB))
+    if (method >= 3 && (!TA || !TB))
         return ED_EINVAL;
     for (size_t i = 0; i < q; i++)
         if (x[i] < 0 || y[i] < 0 || x[i] > (int64_t)n || y[i] > (int64_t)m)
@@ -834,9 +863,12 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
     HashArgs H{};
     H.TA = TA;
     H.TB = TB;
+    // methods 5, 6: 3, 4 on blocked tables with the context's block size
+    H.b = method >= 5 ? ctx->cfg.hash_block : 1;
     std::memcpy(H.pow2, ctx->pow2, sizeof(H.pow2));
     CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, (const int64_t *)ctx->qx.p, (const int64_t *)ctx->qy.p,
-                          (int64_t)q, method, &H, (int64_t *)ctx->qo.p, nullptr, ctx->grid, s));
+                          (int64_t)q, method >= 5 ? method - 2 : method, &H, (int64_t *)ctx->qo.p, nullptr,
+                          ctx->grid, s));
     CK(cudaMemcpyAsync(out, ctx->qo.p, 8 * q, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return ED_OK;

@@ -11,7 +11,9 @@
 // in shared memory, and tiles chain through a decoupled look-back on tile
 // descriptors (aggregate first, inclusive prefix when known), with tile ids
 // handed out in launch order by an atomic counter.  Reads 1 byte and writes
-// 8 bytes per character.
+// 8 bytes per character; with an output stride b > 1 it writes only the
+// prefixes of whole blocks, T[j] = h(X[0..jb)), the blocked table of
+// Sec. 3.3 (Alg. 2), 8/b bytes per character.
 #include "ed_device.cuh"
 #include "lv_kernels.cuh"
 
@@ -50,7 +52,7 @@ __device__ __forceinline__ HPair hcat(HPair a, HPair b)
 }
 
 __global__ void __launch_bounds__(HT) prefix_hash_kernel(const uint8_t *X, int64_t len, uint64_t base,
-                                                         uint64_t *T,
+                                                         uint64_t *T, int64_t stride,
                                                          ScanState *st, uint64_t spin_ns)
 {
     __shared__ HPair s_pair[HT];
@@ -155,21 +157,33 @@ __global__ void __launch_bounds__(HT) prefix_hash_kernel(const uint8_t *X, int64
     uint64_t h = excl.h;
     if (tile == 0 && tid == 0)
         T[0] = 0;
-    for (int i = 0; i < cnt; i++) {
-        h = addmod61(mulmod61(h, base), (uint64_t)c[i] + 1);
-        T[s0 + i + 1] = h;
+    if (stride == 1) {
+        for (int i = 0; i < cnt; i++) {
+            h = addmod61(mulmod61(h, base), (uint64_t)c[i] + 1);
+            T[s0 + i + 1] = h;
+        }
+    } else {
+        // only the prefixes that end a whole block
+        int64_t next = (s0 / stride + 1) * stride; // first block end after s0
+        for (int i = 0; i < cnt; i++) {
+            h = addmod61(mulmod61(h, base), (uint64_t)c[i] + 1);
+            if (s0 + i + 1 == next) {
+                T[next / stride] = h;
+                next += stride;
+            }
+        }
     }
 
 }
 
-cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base,
-                               uint64_t *T, void *scan_state, size_t scan_state_bytes, cudaStream_t s)
+cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T, int64_t stride,
+                               void *scan_state, size_t scan_state_bytes, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(scan_state, 0, scan_state_bytes, s);
     if (e != cudaSuccess)
         return e;
     const int64_t tiles = len == 0 ? 1 : (len + TILE_CHARS - 1) / TILE_CHARS;
-    prefix_hash_kernel<<<(unsigned)tiles, HT, 0, s>>>(X, len, base, T,
+    prefix_hash_kernel<<<(unsigned)tiles, HT, 0, s>>>(X, len, base, T, stride < 1 ? 1 : stride,
                                                       reinterpret_cast<ScanState *>(scan_state),
                                                       2000000000ull);
     return cudaGetLastError();
@@ -228,7 +242,7 @@ extern "C" int ed_prefix_hash_noalloc(const uint8_t *X, size_t len, uint64_t bas
     }
     cudaStream_t s = (cudaStream_t)stream;
     // the look-back descriptors must start at zero: cleared on every call
-    if (edg::launch_prefix_hash(X, (int64_t)len, base, T, scratch, need, s) != cudaSuccess)
+    if (edg::launch_prefix_hash(X, (int64_t)len, base, T, 1, scratch, need, s) != cudaSuccess)
         return ED_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess)
         return ED_ECUDA;

@@ -122,6 +122,7 @@ struct LvArgs {
     int32_t s0;           // initial tile width
     int32_t t2_cap;       // bytes one warp examines before escalating
     int32_t use_hash;
+    int32_t hash_b;       // prefix-table stride: 1 full, > 1 blocked (Alg. 2)
     uint64_t pow2[62];    // p^(2^j) mod 2^61-1 (hash LCP)
     uint64_t spin_ns;     // bound of one wait on a peer's progress
     uint64_t idle_ns;     // bound of a wait that may span other CTAs' work
@@ -172,6 +173,7 @@ int lv_batch_ctas_per_sm(int W); // resident CTAs per SM (registers, shared memo
 // ---------------------------------------------------------------- tests
 struct HashArgs {
     const uint64_t *TA, *TB;
+    int32_t b;            // table stride: 1 full table, > 1 blocked (Alg. 2)
     uint64_t pow2[62];
 };
 // LCP queries by the building blocks: 0 per thread, 1 per warp, 2 whole
@@ -184,7 +186,9 @@ cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, in
                                cudaStream_t s);
 
 // ---------------------------------------------------------------- hash
-cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T,
+// stride 1: T[i] = h(X[0..i)) for i = 0..len; stride b > 1: T[j] = h(X[0..jb))
+// for j = 0..len/b (the blocked table of Sec. 3.3)
+cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T, int64_t stride,
                                void *scan_state, size_t scan_state_bytes, cudaStream_t s);
 size_t prefix_hash_state_bytes(int64_t len);
 

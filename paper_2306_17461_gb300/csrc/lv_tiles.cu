@@ -61,21 +61,45 @@ __device__ __forceinline__ uint64_t powp(const uint64_t *pow2, int64_t e)
     return r;
 }
 
-// h(A[x..x+L)) == h(B[y..y+L)) with h(S2) = h([S1,S2]) - p^|S2| h(S1).
-__device__ __forceinline__ bool hash_eq(const uint64_t *TA, const uint64_t *TB, int64_t x, int64_t y,
-                                        int64_t L, uint64_t P)
+// A prefix-hash table as the LCP search reads it: the full table (b = 1,
+// T[i] = h(X[0..i))) or the blocked one of Sec. 3.3 (T[j] = h(X[0..jb))).
+struct HashView {
+    const uint64_t *T;
+    const uint8_t *X;
+    int32_t b;
+};
+
+// h(X[0..i)): the entry itself, or Alg. 2's GetHash: the prefix of the last
+// whole block at or before i, extended by Horner's rule over the (< b)
+// characters after it (p = pow2[0]).
+__device__ __forceinline__ uint64_t prefix_at(const HashView &V, int64_t i, uint64_t p)
 {
-    const uint64_t a = submod61(__ldg(TA + x + L), mulmod61(__ldg(TA + x), P));
-    const uint64_t b = submod61(__ldg(TB + y + L), mulmod61(__ldg(TB + y), P));
+    if (V.b == 1)
+        return __ldg(V.T + i);
+    const int64_t r = i / V.b;
+    uint64_t h = __ldg(V.T + r);
+    for (int64_t j = r * V.b; j < i; j++)
+        h = addmod61(mulmod61(h, p), (uint64_t)__ldg(V.X + j) + 1);
+    return h;
+}
+
+// h(A[x..x+L)) == h(B[y..y+L)) with h(S2) = h([S1,S2]) - p^|S2| h(S1).
+__device__ __forceinline__ bool hash_eq(const HashView &VA, const HashView &VB, uint64_t p, int64_t x,
+                                        int64_t y, int64_t L, uint64_t P)
+{
+    const uint64_t a = submod61(prefix_at(VA, x + L, p), mulmod61(prefix_at(VA, x, p), P));
+    const uint64_t b = submod61(prefix_at(VB, y + L, p), mulmod61(prefix_at(VB, y, p), P));
     return a == b;
 }
 
-// Sec. 3.2: compare chunks of length 1, 2, 4, ... (here: the powers of two
-// above the l0 bytes already known equal) until one differs, then search
-// the last bracket.  Returns the hash LCP (<= lim); the caller confirms it.
-__device__ __noinline__ int64_t hash_lcp(const uint64_t *pow2, const uint64_t *TA, const uint64_t *TB,
+// Sec. 3.2 (and Alg. 2 on blocked tables): compare chunks of length 1, 2,
+// 4, ... (here: the powers of two above the l0 bytes already known equal)
+// until one differs, then search the last bracket.  Returns the hash LCP
+// (<= lim); the caller confirms it.
+__device__ __noinline__ int64_t hash_lcp(const uint64_t *pow2, const HashView VA, const HashView VB,
                                          int64_t x, int64_t y, int64_t l0, int64_t lim)
 {
+    const uint64_t p = pow2[0];
     int64_t good = l0, bad;
     uint64_t pg = powp(pow2, good);
     int j = 0;
@@ -84,12 +108,12 @@ __device__ __noinline__ int64_t hash_lcp(const uint64_t *pow2, const uint64_t *T
     for (;; j++) {
         const int64_t L = 1ll << j;
         if (L >= lim) {
-            if (hash_eq(TA, TB, x, y, lim, powp(pow2, lim)))
+            if (hash_eq(VA, VB, p, x, y, lim, powp(pow2, lim)))
                 return lim;
             bad = lim;
             break;
         }
-        if (hash_eq(TA, TB, x, y, L, pow2[j])) {
+        if (hash_eq(VA, VB, p, x, y, L, pow2[j])) {
             good = L;
             pg = pow2[j];
         } else {
@@ -103,7 +127,7 @@ __device__ __noinline__ int64_t hash_lcp(const uint64_t *pow2, const uint64_t *T
         const int64_t cand = good + (1ll << i);
         if (cand < bad) {
             const uint64_t P = mulmod61(pg, pow2[i]);
-            if (hash_eq(TA, TB, x, y, cand, P)) {
+            if (hash_eq(VA, VB, p, x, y, cand, P)) {
                 good = cand;
                 pg = P;
             }
@@ -500,7 +524,8 @@ __device__ __forceinline__ void open_bounds(const LvArgs &P, const Pair &Q, cons
     const int64_t full = min(Q.n - cc, Q.m - cc - d);
     int64_t lim = full;
     if (Q.hash && full > 0) {
-        const int64_t h = hash_lcp(P.pow2, Q.TA, Q.TB, cc, cc + d, 0, full);
+        const int64_t h = hash_lcp(P.pow2, HashView{Q.TA, Q.A, P.hash_b}, HashView{Q.TB, Q.B, P.hash_b}, cc,
+                                   cc + d, 0, full);
         C.hashq += own;
         lim = min(h + 1, full);
     }
@@ -702,7 +727,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
     Q.TA = D.TA;
     Q.TB = D.TB;
     Q.hash = P.use_hash && D.TA && D.TB;
-    const int64_t n = Q.n, m = Q.m, target = m - n, nm = max(n, m);
+    const int64_t n = Q.n, m = Q.m, nm = max(n, m);
     const int64_t gstride = 2 * kc + 5;
     const bool leader = (gi == 0 && tid == 0);
     // a pair with a keep buffer may be left at a sync point and resumed
@@ -1058,7 +1083,7 @@ __global__ void lcp_query_kernel(const uint8_t *A, int64_t n, const uint8_t *B, 
                 // the leading window directly, then the doubling search
                 int64_t l = slide_thread(A, n, B, m, x, y, lim, 4, &open);
                 if (open) {
-                    const int64_t hh = hash_lcp(H.pow2, H.TA, H.TB, x, y, l, lim);
+                    const int64_t hh = hash_lcp(H.pow2, HashView{H.TA, A, H.b}, HashView{H.TB, B, H.b}, x, y, l, lim);
                     if (method == 3) {
                         l = hh;
                     } else {

@@ -58,3 +58,32 @@ def test_invalid_arguments_rejected_before_any_cuda_call(lib):
     assert lib.ed_create(None, None) == -1
     assert lib.ed_poll(None, 1, ctypes.byref(k)) == -1
     assert lib.ed_destroy(None) == -1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Field offsets and sizes of ed_config and ed_stats as a C compiler lays
+    them out from include/ed.h equal the ctypes structures of the binding."""
+    import shutil
+    import subprocess
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ed.h"', "int main(void) {"]
+    for sname, cls in [("ed_config", ed.ed_config), ("ed_stats", ed.ed_stats)]:
+        lines.append(f'printf("{sname} size %zu\\n", sizeof({sname}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{sname} {f[0]} %zu\\n", offsetof({sname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for sname, cls in [("ed_config", ed.ed_config), ("ed_stats", ed.ed_stats)]:
+        assert got[(sname, "size")] == ctypes.sizeof(cls), sname
+        for f in cls._fields_:
+            assert got[(sname, f[0])] == getattr(cls, f[0]).offset, (sname, f[0])

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 # kernel configurations exercised: default; narrow first tiles (many epoch
 # changes, the band crosses many tiles); one round per block; odd block
-# lengths and few CTAs; one CTA; the hash LCP
+# lengths and few CTAs; one CTA; the hash LCP on full and on blocked prefix
+# tables (Sec. 3.3; blocks of 32 and of 7 characters)
 CONFIGS = {
     "default": {},
     "wide": {"tile_width": 1, "block_rounds": 4},
@@ -22,6 +23,8 @@ CONFIGS = {
     "one_cta": {"grid_ctas": 1},
     "hash": {"lcp_mode": 2},
     "hash_wide": {"lcp_mode": 2, "tile_width": 1, "block_rounds": 5},
+    "bhash": {"lcp_mode": 3},
+    "bhash_b7_wide": {"lcp_mode": 3, "hash_block": 7, "tile_width": 1, "block_rounds": 5},
 }
 
 

@@ -125,3 +125,44 @@ def test_hash_lcp_matches_direct(ctx, orc, method):
     got = ed.ed_lcp_dev(ctx.h, dA, dB, xs, ys, method, TA, TB)
     want = np.array([orc.lcp(A, B, int(x), int(y)) for x, y in zip(xs, ys)])
     assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------------- blocked (Sec. 3.3, Alg. 2)
+@pytest.mark.parametrize("b", [1, 7, 16, 32, 33, 4096])
+@pytest.mark.parametrize("length", [0, 5, 31, 32, 33, 4095, 4097, 100_003])
+def test_blocked_prefix_hash_matches_oracle(ctx, orc, b, length):
+    """The block prefixes h(X[0..jb)), j = 0..len/b, bit for bit: strides
+    that do and do not divide the 16 characters a thread folds or the 4096
+    of a scan tile, strings shorter than a block, ragged tails."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    rng = np.random.default_rng(1000 * b + length)
+    X = rng.integers(0, 256, length, dtype=np.uint8)
+    base = ed.ed_hash_base(ctx.h)
+    T = ed.ed_prefix_hash_blocked_dev(ctx.h, dev(X), b).cpu().numpy().view(np.uint64)
+    assert np.array_equal(T, orc.prefix_hash_blocked(X, b, base))
+
+
+@pytest.mark.parametrize("method", [5, 6])
+def test_blocked_hash_lcp_matches_oracle(orc, method):
+    """Methods 5 (search alone) and 6 (confirmed) on blocked tables: equal to
+    the oracle's blocked search and to the character LCP."""
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    with ed.Context(device=0, hash_block=32) as c:
+        rng = np.random.default_rng(70 + method)
+        A, B, xs, ys = _lcp_cases(rng)
+        dA, dB = dev(A), dev(B)
+        TA = ed.ed_prefix_hash_blocked_dev(c.h, dA, 32)
+        TB = ed.ed_prefix_hash_blocked_dev(c.h, dB, 32)
+        torch.cuda.synchronize()
+        got = ed.ed_lcp_dev(c.h, dA, dB, xs, ys, method, TA, TB)
+        base = ed.ed_hash_base(c.h)
+        hA, hB = TA.cpu().numpy().view(np.uint64), TB.cpu().numpy().view(np.uint64)
+        want = np.array([orc.lcp(A, B, int(x), int(y)) for x, y in zip(xs, ys)])
+        if method == 5:
+            ob = np.array([orc.hash_lcp_blocked(A, hA, B, hB, 32, base, int(x), int(y)) for x, y in zip(xs, ys)])
+            assert np.array_equal(ob, want)  # no collision on these inputs
+        assert np.array_equal(got, want)
