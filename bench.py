@@ -181,6 +181,8 @@ def profile_traffic(name: str):
 
 
 # ------------------------------------------------------------------ workloads
+DEFAULT_KS = "10,1000,100000"
+
 def make_workload(name: str, args):
     from paper_2306_17461_gb300 import workloads as W
 
@@ -194,6 +196,12 @@ def make_workload(name: str, args):
     elif name == "large":
         pairs = [W.single_large(n=args.n or 10**9)]
         desc = "single pair, n=1e9 Zipf(1.1) over 256 symbols, 1e4 edits in geometric bursts"
+    elif name == "lcplen":
+        ks = [int(x) for x in (args.ks if args.ks != DEFAULT_KS else "10000,50000").split(",")]
+        skews = [float(x) for x in args.skews.split(",")]
+        pairs = [W.lcp_length_pair(k, p0, n=args.n or 10**7) for k in ks for p0 in skews]
+        desc = (f"Fig. 4 setting: n={args.n or 10**7}, two symbols with P(0) in {skews}, "
+                f"planted k in {ks}, one launch per pair")
     else:
         raise ValueError(name)
     return pairs, desc
@@ -225,20 +233,30 @@ def run_single(args, D: Dist):
     for _ in range(args.warmup):
         step()
     recs = []
+    # inputs smaller than L2 (129 MB): flush it between timed steps by
+    # writing 256 MB, outside the steps' events
+    in_bytes = sum(int(p.A.size + p.B.size) for p in pairs)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if in_bytes < (256 << 20) else None
+    l2_note = ("flushed between steps (256 MB written outside the timed events)" if flush is not None
+               else "no flush: each pair's strings (>= 2e8 B) exceed the 129 MB L2")
     D.barrier()
     torch.cuda.synchronize()
     clocks = Clocks(D.local)
     clocks.start()
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
+    evs = []
+    for i in range(args.steps):
+        if flush is not None:
+            flush.fill_(i & 255)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         step(recs)
-    ev1.record(stream)
+        e1.record(stream)
+        evs.append((e0, e1))
     torch.cuda.synchronize()
     D.barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     ext = sum(r[2]["extensions"] for r in recs)
     cbytes = sum(r[2]["compared_bytes"] for r in recs)
     kms = sum(r[2]["kernel_ms"] for r in recs)
@@ -249,7 +267,9 @@ def run_single(args, D: Dist):
                                "ms": [], "ext": st["extensions"], "compared_bytes": st["compared_bytes"],
                                "long_slides": st["long_slides"], "open_slides": st["open_slides"],
                                "wide_rounds": st["wide_rounds"],
-                               "phase_ms": [round(x, 3) for x in st["phase_ms"]], "build_ms": []})
+                               "phase_ms": [round(x, 3) for x in st["phase_ms"]], "build_ms": [],
+                               # the mean LCP length of the slides (Fig. 4's x axis)
+                               "avg_lcp": st["slide_chars"] / max(1, st["extensions"])})
         d["ms"].append(st["kernel_ms"])
         d["build_ms"].append(st["build_ms"])
     for d in per.values():
@@ -289,7 +309,7 @@ def run_single(args, D: Dist):
         "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": desc, "lcp": args.lcp, "pairs_per_step": len(pairs),
-                   "l2": "no flush: each pair's strings (>= 2e8 B) exceed the 129 MB L2",
+                   "l2": l2_note,
                    "parallelism": f"replicas x{D.ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
@@ -521,9 +541,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="mid", choices=["mid", "small", "large", "batch", "serve"])
+    ap.add_argument("--workload", default="mid", choices=["mid", "small", "large", "batch", "serve", "lcplen"])
     ap.add_argument("--lcp", default="direct", choices=["direct", "hash", "bhash"])
-    ap.add_argument("--ks", default="10,1000,100000")
+    ap.add_argument("--ks", default=DEFAULT_KS)
+    ap.add_argument("--skews", default="0.5,0.9,0.99,0.999,0.9999")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--npairs", type=int, default=4096)
     ap.add_argument("--npairs-serve", type=int, default=128)

@@ -29,6 +29,10 @@ The five workloads (seed = 20230617 + workload index):
    [10^-4, 5*10^-2], uniform positions.
 5. ``serve``         -- 512 pairs, n log-uniform on [10^2, 10^7], sigma 4,
    edit rate log-uniform on [10^-3, 10^-1]; Poisson arrival times.
+6. ``lcp_length``    -- the setting of Fig. 4: n = 10^7, k in {10^4,
+   5*10^4}, two symbols with P(symbol 0) = p0 skewed so that chance matches
+   run long (two random positions agree with probability
+   q = p0^2 + (1-p0)^2, a mean run of q / (1 - q)); uniform edits.
 """
 from __future__ import annotations
 
@@ -62,9 +66,14 @@ def _zipf_lut(s: float = 1.1, sigma: int = 256) -> np.ndarray:
 
 
 class Symbols:
-    """A symbol distribution: uniform over sigma bytes, or Zipf over 256."""
+    """A symbol distribution: uniform over sigma bytes, Zipf over 256, or
+    two symbols with P(0) = p0 (through a 65536-entry lookup table)."""
 
-    def __init__(self, sigma: int = 4, zipf_s: float | None = None):
+    def __init__(self, sigma: int = 4, zipf_s: float | None = None, p0: float | None = None):
+        if p0 is not None:
+            self.sigma = 2
+            self.lut = (np.arange(65536) >= int(round(p0 * 65536))).astype(np.uint8)
+            return
         self.sigma = 256 if zipf_s is not None else sigma
         self.lut = _zipf_lut(zipf_s) if zipf_s is not None else None
 
@@ -81,6 +90,8 @@ class Symbols:
 
     def draw_unlike(self, rng: np.random.Generator, old: np.ndarray) -> np.ndarray:
         """One drawn symbol per entry of ``old``, each different from it."""
+        if self.sigma == 2: # the only other symbol
+            return (1 - old).astype(np.uint8)
         new = self.draw(rng, old.size)
         bad = new == old
         while bad.any():
@@ -216,3 +227,14 @@ def random_pair(rng: np.random.Generator, n: int, k: int, sigma: int) -> tuple[n
     A = sym.draw(rng, n)
     B = plant(rng, A, uniform_positions(rng, n, k), sym)
     return A, B
+
+
+def lcp_length_pair(k: int, p0: float, n: int = 10**7, extra: int = 0) -> Pair:
+    """Fig. 4's setting: n characters over two symbols with P(0) = p0, k
+    uniform planted edits (seed 20230617 + 6)."""
+    rng = rng_for(6, extra + int(round(p0 * 1e6)) * 7 + k)
+    sym = Symbols(p0=p0)
+    A = sym.draw(rng, n)
+    pos = uniform_positions(rng, n, k)
+    B = plant(rng, A, pos, sym)
+    return Pair(A, B, int(np.unique(pos).size), f"n={n} k_planted={k} binary p0={p0}")

@@ -184,3 +184,28 @@ def test_band_outgrows_tiles_and_resumes(orc):
         assert st["kernel_launches"] == 3
         # every round counted once: a resumed launch starts where the last stopped
         assert st["extensions"] == orc.lv(p.A, p.B, with_stats=True)[2]
+
+
+@pytest.mark.parametrize("p0", [0.5, 0.9, 0.99])
+def test_lcp_length_workload_reduced(ctxs, orc, p0):
+    """Fig. 4's inputs (two skewed symbols, long chance matches) at n = 2e5:
+    every LCP mode gives the oracle's distance."""
+    from paper_2306_17461_gb300 import binding as ed
+
+    for k in (300, 1000):
+        p = W.lcp_length_pair(k, p0, n=200_000)
+        want = orc.lv(p.A, p.B)
+        for cfg in ("default", "hash", "bhash"):
+            assert ctxs[cfg].distance_dev(dev(p.A), dev(p.B)) == want, (cfg, k, p0)
+
+
+def test_skew_lengthens_the_slides(ctxs):
+    """Fig. 4's x axis: the mean LCP per diagonal-extension grows with the
+    skew of the two symbols."""
+    means = []
+    for p0 in (0.5, 0.9, 0.99):
+        p = W.lcp_length_pair(1000, p0, n=200_000)
+        ctxs["default"].distance_dev(dev(p.A), dev(p.B))
+        st = ctxs["default"].stats()
+        means.append(st["slide_chars"] / st["extensions"])
+    assert means[0] < means[1] < means[2], means

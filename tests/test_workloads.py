@@ -51,3 +51,23 @@ def test_poisson_arrivals():
     t = W.poisson_arrivals(10.0, 5000)
     assert np.all(np.diff(t) > 0)
     assert abs(t[-1] / 5000 - 0.1) < 0.01
+
+
+def test_lcp_length_pairs_are_skewed_binary_and_seeded():
+    from paper_2306_17461_gb300 import workloads as W
+
+    for p0 in (0.5, 0.9, 0.99):
+        p = W.lcp_length_pair(200, p0, n=200_000)
+        assert set(np.unique(p.A).tolist()) <= {0, 1} and set(np.unique(p.B).tolist()) <= {0, 1}
+        assert abs((p.A == 0).mean() - p0) < 0.01
+        assert p.edits == 200 and abs(p.B.size - p.A.size) <= 200
+        q = W.lcp_length_pair(200, p0, n=200_000)
+        assert np.array_equal(p.A, q.A) and np.array_equal(p.B, q.B)
+
+
+def test_binary_substitution_flips_the_symbol():
+    from paper_2306_17461_gb300 import workloads as W
+
+    sym = W.Symbols(p0=0.999)
+    old = np.array([0, 1, 0, 0, 1], dtype=np.uint8)
+    assert sym.draw_unlike(np.random.default_rng(0), old).tolist() == [1, 0, 1, 1, 0]
