@@ -217,7 +217,7 @@ def run_single(args, D: Dist):
     dev = torch.device("cuda", D.local)
     pairs, desc = make_workload(args.workload, args)
     lcp_mode = {"direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH, "bhash": ed.ED_LCP_BHASH}[args.lcp]
-    ctx = ed.Context(device=D.local, lcp_mode=lcp_mode)
+    ctx = ed.Context(device=D.local, lcp_mode=lcp_mode, block_rounds=args.block_rounds)
     dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
     dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
     stream = torch.cuda.current_stream()
@@ -545,6 +545,7 @@ def main():
     ap.add_argument("--lcp", default="direct", choices=["direct", "hash", "bhash"])
     ap.add_argument("--ks", default=DEFAULT_KS)
     ap.add_argument("--skews", default="0.5,0.9,0.99,0.999,0.9999")
+    ap.add_argument("--block-rounds", type=int, default=0, help="rounds per temporal block (0: 16)")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--npairs", type=int, default=4096)
     ap.add_argument("--npairs-serve", type=int, default=128)
