@@ -65,21 +65,25 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
     const int32_t *prev = R.prev;
     int32_t *cur = R.cur;
     uint32_t slide = 0, mism = 0;
+    // byte phases of the two strings' bases within a 4-byte word
+    const uint32_t pa0 = (uint32_t)(uintptr_t)R.A, pb0 = (uint32_t)(uintptr_t)R.B;
     for (int32_t base = lo; base <= hi; base += nt * DPT) {
         int32_t c[DPT];
+        uint32_t sh[DPT]; // byte offsets of A[c] and B[c+d] in their words: sa | sb << 8
         uint2 wa[DPT], wb[DPT];
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
             const int32_t d = base + u * nt + tid;
             c[u] = -1;
+            sh[u] = 0;
             wa[u] = wb[u] = make_uint2(0u, 0u);
             if (d <= hi) {
                 int32_t cc = 0;
                 if (!first) {
                     const int32_t x1 = prev[d - 1 - off];
-                    const int32_t x2 = prev[d - off] + 1;
-                    const int32_t x3 = prev[d + 1 - off] + 1;
-                    cc = min(max(x1, max(x2, x3)), d <= mn ? n : m - d);
+                    const int32_t x2 = prev[d - off];
+                    const int32_t x3 = prev[d + 1 - off];
+                    cc = min(max(x1, max(x2, x3) + 1), d <= mn ? n : m - d);
                 }
                 if (cc < 0 || cc + d < 0) {
                     // a start row outside the grid: record it, never load it
@@ -95,8 +99,20 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
                     }
                 } else {
                     c[u] = cc;
-                    if (min(n - cc, m - cc - d) > 0)
-                        word_load2(R.A, n, R.B, m, cc, cc + d, wa[u], wb[u]);
+                    if (min(n - cc, m - cc - d) > 0) {
+                        // the aligned word holding A[cc] and the next one (only
+                        // while it still holds a byte of A: then it cannot
+                        // fault); the same for B[cc + d]
+                        const int32_t ya = cc, yb = cc + d;
+                        const uint32_t sa = (pa0 + (uint32_t)ya) & 3u, sb = (pb0 + (uint32_t)yb) & 3u;
+                        const uint32_t *qa = reinterpret_cast<const uint32_t *>(R.A + (ya - (int32_t)sa));
+                        const uint32_t *qb = reinterpret_cast<const uint32_t *>(R.B + (yb - (int32_t)sb));
+                        wa[u].x = __ldg(qa);
+                        wb[u].x = __ldg(qb);
+                        wa[u].y = ya - (int32_t)sa + 4 < n ? __ldg(qa + 1) : 0u;
+                        wb[u].y = yb - (int32_t)sb + 4 < m ? __ldg(qb + 1) : 0u;
+                        sh[u] = sa | (sb << 8);
+                    }
                 }
             }
         }
@@ -106,7 +122,20 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
             if (d <= hi && c[u] >= 0) {
                 const int32_t cc = c[u];
                 const int32_t full = min(n - cc, m - cc - d);
-                const int32_t l = (int32_t)word_slide2(R.A, R.B, cc, cc + d, full, wa[u], wb[u]);
+                // the bytes from A[cc] and B[cc + d] the two words hold: 8 - max(sa, sb)
+                // (at least five); the first four by funnel shift, the rest after
+                const uint32_t sa = sh[u] & 255u, sb = sh[u] >> 8;
+                const uint32_t smax = max(sa, sb);
+                const uint32_t m1 = __funnelshift_r(wa[u].x, wa[u].y, 8 * sa) ^ __funnelshift_r(wb[u].x, wb[u].y, 8 * sb);
+                const uint32_t m2 = ((wa[u].y >> (8 * sa)) ^ (wb[u].y >> (8 * sb))) & (0xffffffffu >> (8 * smax));
+                const int32_t av = 8 - (int32_t)smax;
+                int32_t l = m1 ? (__ffs((int)m1) - 1) >> 3 : (m2 ? 4 + ((__ffs((int)m2) - 1) >> 3) : av);
+                if (full <= 0)
+                    l = 0;
+                else if (l >= full)
+                    l = full;
+                else if (l == av)
+                    l = -1; // every byte the words hold matched: a warp goes on
                 if (l >= 0) {
                     cur[d - off] = cc + l;
                     if (d >= a && d < b) {
