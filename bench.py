@@ -437,8 +437,34 @@ def run_serve(args, D: Dist):
                     "p50_ms": float(np.percentile(L, 50)), "p99_ms": float(np.percentile(L, 99)),
                     "span_s": span})
         log(f"serve rate {rate}: {out[-1]}")
+    # capacity: every request submitted at once, served concurrently
+    t0 = time.perf_counter()
+    tickets = {}
+    i = 0
+    while i < len(pairs) or tickets:
+        while i < len(pairs):
+            try:
+                tickets[ed.ed_submit(ctx.h, pairs[i].A, pairs[i].B)] = i
+                i += 1
+            except ed.EdError as e:
+                if e.code != ed.ED_EBUSY:
+                    raise
+                break
+        for t in list(tickets):
+            if ed.ed_poll(ctx.h, t)[0] == ed.ED_OK:
+                tickets.pop(t)
+        time.sleep(0.0002)
+    capacity = len(pairs) / (time.perf_counter() - t0)
     cnt = ed.ed_serve_counters(ctx.h)
     ctx.close()
+    # the same pairs one at a time through the synchronous call (host strings)
+    one = ed.Context(device=D.local)
+    t0 = time.perf_counter()
+    for p in pairs:
+        ed.ed_distance(one.h, p.A, p.B)
+    one_rate = len(pairs) / (time.perf_counter() - t0)
+    one.close()
+    log(f"serve capacity {capacity:.2f} pairs/s, one at a time {one_rate:.2f} pairs/s")
     best = max(out, key=lambda r: r["pairs_per_s"])
     res = {
         "metric": "served pairs/s",
@@ -458,6 +484,9 @@ def run_serve(args, D: Dist):
         "sweep": out,
         "p50_ms": best["p50_ms"],
         "p99_ms": best["p99_ms"],
+        "capacity_pairs_per_s": capacity,
+        "one_at_a_time_pairs_per_s": one_rate,
+        "speedup_vs_one_at_a_time": capacity / one_rate,
         "engine_steps": cnt["steps"],
         "tile_slices": cnt["slices"],
     }

@@ -166,3 +166,35 @@ def test_blocked_hash_lcp_matches_oracle(orc, method):
             ob = np.array([orc.hash_lcp_blocked(A, hA, B, hB, 32, base, int(x), int(y)) for x, y in zip(xs, ys)])
             assert np.array_equal(ob, want)  # no collision on these inputs
         assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("blocked", [False, True])
+def test_confirmation_makes_wrong_hash_answers_exact(orc, blocked):
+    """The safety net for hash collisions (Sec. 2 remark): every hash answer
+    is confirmed by a direct compare.  Tables of A and B built with two
+    different bases disagree on equal substrings, so the hash search alone
+    answers wrongly on most queries; confirmed, every answer is the
+    character LCP."""
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    rng = np.random.default_rng(77 + blocked)
+    A, B, xs, ys = _lcp_cases(rng)
+    dA, dB = dev(A), dev(B)
+    with ed.Context(device=0, hash_seed=1, hash_block=32) as c1, ed.Context(device=0, hash_seed=2) as c2:
+        if blocked:
+            TA = ed.ed_prefix_hash_blocked_dev(c1.h, dA, 32)
+            TB = ed.ed_prefix_hash_blocked_dev(c2.h, dB, 32)
+            alone, confirmed = 5, 6
+        else:
+            TA = ed.ed_prefix_hash_dev(c1.h, dA)
+            TB = ed.ed_prefix_hash_dev(c2.h, dB)
+            alone, confirmed = 3, 4
+        torch.cuda.synchronize()
+        want = np.array([orc.lcp(A, B, int(x), int(y)) for x, y in zip(xs, ys)])
+        wrong = ed.ed_lcp_dev(c1.h, dA, dB, xs, ys, alone, TA, TB)
+        reach = want >= 8  # queries the leading direct window does not settle
+        assert reach.sum() > 20 and (wrong[reach] != want[reach]).mean() > 0.5  # the tables disagree
+        got = ed.ed_lcp_dev(c1.h, dA, dB, xs, ys, confirmed, TA, TB)
+        assert np.array_equal(got, want)
