@@ -92,7 +92,9 @@ typedef struct {
     double phase_ms[6];      /* device time by phase, as seen by the first
                                 CTA of the group: rounds, open slides,
                                 neighbour waits (helping included), epoch
-                                changes; [4], [5] unused */
+                                changes; [4] the CTAs' average busy time
+                                (rounds + open slides); [5] the batch
+                                kernel's time (batched calls) */
 } ed_stats;
 
 /* Fills *cfg with the defaults described in ed_config. */

@@ -937,11 +937,14 @@ static TileJob parked_job(ed_ctx *ctx, const BatchPair &b)
 }
 
 // While the groups the jobs ask for fill at most half of the grid, doubles
-// them: with few pairs, more CTAs per pair shorten each round.  The cost of
-// a job (for sharing CTAs among classes) is its estimated distance times
-// the round time, which grows with the band per CTA.
+// them: with few pairs, more CTAs per pair shorten each round; a single job
+// takes the whole grid.  The cost of a job (for sharing CTAs among classes)
+// is its estimated distance times the round time, which grows with the band
+// per CTA.
 static void spread_jobs(ed_ctx *ctx, std::vector<TileJob> &jobs)
 {
+    if (jobs.size() == 1)
+        jobs[0].G = ctx->grid;
     for (;;) {
         int64_t sum = 0;
         bool room = false;
@@ -986,6 +989,7 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
                      [&](int32_t a, int32_t b) { return std::max(n[a], m[a]) > std::max(n[b], m[b]); });
     if ((r = batch_launch(ctx, hp, order, ctx->bpairs, ctx->border, ctx->bnext, s, 0)) != ED_OK)
         return r;
+    const double batch_ms = ctx->last.kernel_ms;
     uint64_t ext = 0, slide = 0, mism = 0;
     std::vector<size_t> parked;
     for (size_t p = 0; p < np; p++) {
@@ -1026,6 +1030,7 @@ static int batch_core(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
     ctx->last.extensions = ext;
     ctx->last.slide_chars = slide;
     ctx->last.compared_bytes = 2 * (slide + mism);
+    ctx->last.phase_ms[5] = batch_ms;
     return ED_OK;
 }
 
@@ -1095,13 +1100,14 @@ static void release_request(ed_ctx *ctx, Request *q)
 }
 
 // Moves a request to the tile kernel on a group of G CTAs, with a resident
-// frontier as wide as that group's tiles (none if the arena is full: the
-// pair then runs to its end in one launch).
+// frontier as wide as the whole grid's tiles (so that the pair can change
+// groups between steps; none if the arena is full: the pair then runs to
+// its end in one launch).
 static void to_tiles(ed_ctx *ctx, Request *q, int G)
 {
     ctx->arena.release(q->keep, q->bytesK);
     q->tile_G = G;
-    q->keep_r = std::min<int64_t>(std::max(q->n, q->m), (int64_t)G * SMAX_LIMIT);
+    q->keep_r = std::min<int64_t>(std::max(q->n, q->m), (int64_t)ctx->grid * SMAX_LIMIT);
     q->bytesK = sizeof(int32_t) * (size_t)(2 * q->keep_r + 5);
     q->keep = ctx->arena.alloc(q->bytesK);
     q->t0 = 0;
@@ -1159,9 +1165,6 @@ static void engine_loop(ed_ctx *ctx)
             std::rotate(order.begin(), order.begin() + (ctx->n_steps * grid) % bidx.size(), order.end());
             const int rc = batch_launch(ctx, hp, order, ctx->s_pairs, ctx->s_order, ctx->s_next, ctx->sstream,
                                         SERVE_BATCH_NS);
-            int64_t tile_sum = 0;
-            for (size_t i = 0; i < L; i++)
-                tile_sum += ctx->live[i]->tile_G;
             for (size_t j = 0; j < bidx.size(); j++) {
                 Request *q = ctx->live[bidx[j]];
                 const BatchPair &b = hp[j];
@@ -1174,14 +1177,11 @@ static void engine_loop(ed_ctx *ctx)
                 } else if (b.state == 2) {
                     // group from the distance estimate, doubled while the
                     // tile pairs would fill at most half of the grid
+                    // the group its estimated band needs; each step spreads
+                    // the groups over the grid
                     const TileJob pj = parked_job(ctx, b);
-                    int G = pj.G;
-                    while (G < ctx->grid && 2 * (tile_sum + 2 * G) <= ctx->grid)
-                        G *= 2;
-                    G = std::min(G, ctx->grid);
-                    tile_sum += G;
                     q->cost = pj.cost;
-                    to_tiles(ctx, q, G);
+                    to_tiles(ctx, q, pj.G);
                 } else {
                     q->t = b.t;
                 }
@@ -1205,6 +1205,11 @@ static void engine_loop(ed_ctx *ctx)
             jobs.push_back(j);
         }
         if (!jobs.empty()) {
+            // each pair's group at least what its band needs (tile_G), all of
+            // them spread over the grid (a single pair takes all of it: its
+            // resident frontier holds any group's band)
+            if (std::all_of(jobs.begin(), jobs.end(), [](const TileJob &j) { return j.keep != nullptr; }))
+                spread_jobs(ctx, jobs);
             std::vector<TileOut> o;
             const int rt = run_tiles_once(ctx, jobs, ctx->sstream, SERVE_TILE_NS, o);
             for (size_t j = 0; j < tidx.size(); j++) {
@@ -1219,6 +1224,11 @@ static void engine_loop(ed_ctx *ctx)
                     q->t0 = o[j].rt;
                     q->R0 = o[j].rr;
                     ctx->n_slices++;
+                } else if (o[j].st == ST_WIDE && q->keep && o[j].rt > 0 && jobs[j].G < ctx->grid) {
+                    // a larger group from the saved round
+                    q->tile_G = std::min(ctx->grid, 2 * jobs[j].G);
+                    q->t0 = o[j].rt;
+                    q->R0 = o[j].rr;
                 } else if (o[j].st == ST_WIDE && q->tile_G < ctx->grid) {
                     to_tiles(ctx, q, std::min(ctx->grid, 2 * q->tile_G)); // again, from round 0
                 } else {
