@@ -168,6 +168,12 @@ __global__ void __launch_bounds__(BT, 2) lv_batch_kernel(BatchArgs Bg, uint64_t 
             RA.open = S.ld;
             RA.err = S.err;
             RA.diag = S.diag;
+            RA.tid = tid;
+            RA.nt = nt;
+            RA.open_c = nullptr;
+            RA.ocap = 0;
+            RA.defer = nullptr;
+            RA.nd = nullptr;
             const RoundCount rc = tile_round<4>(RA);
             slide += rc.slide;
             mism += rc.mism;

@@ -15,6 +15,10 @@
 
 namespace edg {
 
+// The frontier value of a diagonal whose slide a warp is still finishing
+// (pipelined rounds): below the minus infinity of undefined diagonals.
+constexpr int32_t PENDING = INT32_MIN;
+
 struct RoundArgs {
     const uint8_t *A, *B;
     int64_t n, m;
@@ -25,6 +29,16 @@ struct RoundArgs {
     int32_t *open;           // diagonals whose slide is still open
     uint32_t *err;           // launch status word (self-check records)
     unsigned long long *diag;
+    int tid, nt;             // this thread among the nt that run the round
+    // pipelined rounds only: the start rows of the open list (ocap entries at
+    // most), and the diagonals deferred because a predecessor is PENDING
+    int32_t *open_c;
+    int ocap;
+    int32_t *defer;
+    int *nd;
+    // list mode: the diagonals list[0..nlist) instead of [lo, hi]
+    const int32_t *list;
+    int nlist;
 };
 struct RoundCount {
     unsigned long long slide, mism;
@@ -53,11 +67,25 @@ __device__ __forceinline__ int64_t start_row(const int32_t *prev, int64_t off, i
 // 2^31 bytes), so the round works in 32-bit integers; the one quantity that
 // can exceed that, m - d (up to n + m), appears only in the clamp, which
 // takes n whenever d <= m - n.
-template <int DPT> // diagonals per thread per batch
+// An open slide that found the open list full finishes here, one thread,
+// 16-byte windows: only for inputs where more than ocap slides of a round
+// stay open (long common runs on every diagonal).
+static __device__ __noinline__ int32_t slide_alone(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int32_t c,
+                                            int32_t d, int32_t full)
+{
+    bool open;
+    return (int32_t)slide_thread(A, n, B, m, c, (int64_t)c + d, full, INT64_MAX, &open);
+}
+
+// PIPE: the pipelined form of the tile kernel.  A diagonal with a PENDING
+// predecessor is deferred (listed in R.defer) instead of computed; an open
+// slide is listed with its start row (R.open, R.open_c) and its value set to
+// PENDING until a warp finishes it.
+template <int DPT, bool PIPE = false, bool LIST = false> // DPT: diagonals per thread per batch
 __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
 {
     RoundCount out = {0, 0};
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = R.tid, nt = R.nt;
     const int32_t n = (int32_t)R.n, m = (int32_t)R.m, mn = (int32_t)(R.m - R.n);
     const int32_t off = (int32_t)R.off, lo = (int32_t)R.lo, hi = (int32_t)R.hi;
     const int32_t a = (int32_t)R.a, b = (int32_t)R.b;
@@ -67,25 +95,34 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
     uint32_t slide = 0, mism = 0;
     // byte phases of the two strings' bases within a 4-byte word
     const uint32_t pa0 = (uint32_t)(uintptr_t)R.A, pb0 = (uint32_t)(uintptr_t)R.B;
-    for (int32_t base = lo; base <= hi; base += nt * DPT) {
+    const int32_t first_slot = LIST ? 0 : lo, last_slot = LIST ? R.nlist - 1 : hi;
+    for (int32_t base = first_slot; base <= last_slot; base += nt * DPT) {
         int32_t c[DPT];
         uint32_t sh[DPT]; // byte offsets of A[c] and B[c+d] in their words: sa | sb << 8
         uint2 wa[DPT], wb[DPT];
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
-            const int32_t d = base + u * nt + tid;
+            const int32_t slot = base + u * nt + tid;
+            const int32_t d = LIST ? (slot <= last_slot ? R.list[slot] : 0) : slot;
             c[u] = -1;
             sh[u] = 0;
             wa[u] = wb[u] = make_uint2(0u, 0u);
-            if (d <= hi) {
+            if (slot <= last_slot) {
                 int32_t cc = 0;
+                bool blocked = false;
                 if (!first) {
                     const int32_t x1 = prev[d - 1 - off];
                     const int32_t x2 = prev[d - off];
                     const int32_t x3 = prev[d + 1 - off];
+                    if (PIPE && min(x1, min(x2, x3)) == PENDING) {
+                        R.defer[atomicAdd(R.nd, 1)] = d;
+                        blocked = true;
+                    }
                     cc = min(max(x1, max(x2, x3) + 1), d <= mn ? n : m - d);
                 }
-                if (cc < 0 || cc + d < 0) {
+                if (blocked) {
+                    // computed later, from the finished value
+                } else if (cc < 0 || cc + d < 0) {
                     // a start row outside the grid: record it, never load it
                     if (atomicCAS(R.err, 0u, 6u) == 0u) {
                         R.diag[0] = 6;
@@ -118,8 +155,9 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
         }
 #pragma unroll
         for (int u = 0; u < DPT; u++) {
-            const int32_t d = base + u * nt + tid;
-            if (d <= hi && c[u] >= 0) {
+            const int32_t slot = base + u * nt + tid;
+            const int32_t d = LIST ? (slot <= last_slot ? R.list[slot] : 0) : slot;
+            if (slot <= last_slot && c[u] >= 0) {
                 const int32_t cc = c[u];
                 const int32_t full = min(n - cc, m - cc - d);
                 // the bytes from A[cc] and B[cc + d] the two words hold: 8 - max(sa, sb)
@@ -142,8 +180,22 @@ __device__ __forceinline__ RoundCount tile_round(const RoundArgs &R)
                         slide += (uint32_t)l;
                         mism += (l < full);
                     }
-                } else {
+                } else if (!PIPE) {
                     R.open[atomicAdd(R.n1, 1)] = d;
+                } else {
+                    const int j = atomicAdd(R.n1, 1);
+                    if (j < R.ocap) {
+                        R.open[j] = d;
+                        R.open_c[j] = cc;
+                        cur[d - off] = PENDING;
+                    } else {
+                        const int32_t l2 = slide_alone(R.A, n, R.B, m, cc, d, full);
+                        cur[d - off] = cc + l2;
+                        if (d >= a && d < b) {
+                            slide += (uint32_t)l2;
+                            mism += (l2 < full);
+                        }
+                    }
                 }
             }
         }

@@ -207,6 +207,10 @@ __device__ __noinline__ void wait_failed(const LvArgs &P, unsigned long long sit
 struct Smem {
     int32_t *F0, *F1;   // tile + halo frontier, smax + 2*HMAX + 2 entries each
     int32_t *ld;        // open slides: diagonal (lcap entries)
+    // pipelined rounds: open lists by round parity (diagonal, start row;
+    // OCAP entries each) and their counts, the deferred diagonals of a round
+    int32_t *Ld0, *Ld1, *Lc0, *Lc1, *D;
+    int *nL, *nD;
     int *n1;
     int *bc;            // 8 broadcast words
     long long *bcl;     // 4 broadcast 64-bit words
@@ -454,11 +458,16 @@ __device__ bool group_sync(const LvArgs &P, GroupCtl *gc, int G, const Smem S)
     return group_barrier(P, gc, &gc->bar_count, &gc->bar_gen, G, false, S) == 1;
 }
 
+constexpr int OCAP = 1024;     // open slides listed per round (pipelined rounds)
+constexpr int DCAP = 3 * OCAP; // deferred diagonals: neighbours of open ones
+
 size_t lv_tiles_smem_bytes(int smax, int h)
 {
     (void)h;
-    // two frontier buffers and the open-slide list, each smax + 2*HMAX + 2
-    return 128 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2);
+    // two frontier buffers and the open-slide list, each smax + 2*HMAX + 2;
+    // two open lists of OCAP (diagonal, start row); DCAP deferred diagonals
+    return 256 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2) +
+           sizeof(int32_t) * (4 * (size_t)OCAP + DCAP);
 }
 
 // The frontier of round r (buffers alternate by parity).
@@ -473,13 +482,21 @@ __device__ Smem carve(const LvArgs &P)
     S.bcl = reinterpret_cast<long long *>(p + 16);
     S.n1 = reinterpret_cast<int *>(p + 64);
     S.bc = S.n1 + 4;
-    p += 128;
+    S.nL = reinterpret_cast<int *>(p + 128);
+    S.nD = S.nL + 2;
+    p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * S.lcap;
     S.F0 = reinterpret_cast<int32_t *>(p);
     p += sizeof(int32_t) * (P.smax + 2 * HMAX + 2);
     S.F1 = reinterpret_cast<int32_t *>(p);
+    p += sizeof(int32_t) * (P.smax + 2 * HMAX + 2);
+    S.Ld0 = reinterpret_cast<int32_t *>(p);
+    S.Ld1 = S.Ld0 + OCAP;
+    S.Lc0 = S.Ld1 + OCAP;
+    S.Lc1 = S.Lc0 + OCAP;
+    S.D = S.Lc1 + OCAP;
     S.err = &P.ctl->error;
     S.diag = P.ctl->diag;
     return S;
@@ -514,71 +531,68 @@ __device__ __forceinline__ int32_t *halo_ptr(const LvArgs &P, int cta, int parit
     return P.halo + ((int64_t)(cta * 2 + parity) * 2 + side) * HMAX;
 }
 
-// The slide of open diagonal d: its start row c and the bound lim_abs of
-// its first mismatch (the string end, or the hash answer + 1).
-__device__ __forceinline__ void open_bounds(const LvArgs &P, const Pair &Q, const int32_t *prev, int64_t off,
-                                            int64_t tau, int64_t d, int64_t *c, int64_t *lim_abs, Counters &C,
-                                            bool own)
+// The bound of an open slide of diagonal d from row c: the string end, or
+// the hash answer + 1 (the slide confirms it directly).
+__device__ __forceinline__ int64_t open_limit(const LvArgs &P, const Pair &Q, int64_t c, int64_t d, Counters &C,
+                                              bool own)
 {
-    const int64_t cc = start_row(prev, off, d, tau, Q.n, Q.m);
-    const int64_t full = min(Q.n - cc, Q.m - cc - d);
+    const int64_t full = min(Q.n - c, Q.m - c - d);
     int64_t lim = full;
     if (Q.hash && full > 0) {
-        const int64_t h = hash_lcp(P.pow2, HashView{Q.TA, Q.A, P.hash_b}, HashView{Q.TB, Q.B, P.hash_b}, cc,
-                                   cc + d, 0, full);
+        const int64_t h = hash_lcp(P.pow2, HashView{Q.TA, Q.A, P.hash_b}, HashView{Q.TB, Q.B, P.hash_b}, c,
+                                   c + d, 0, full);
         C.hashq += own;
         lim = min(h + 1, full);
     }
-    *c = cc;
-    *lim_abs = cc + lim;
+    return c + lim;
 }
 
-// Open slides of one round: one warp each (t2_cap bytes, which finishes
-// most of them in one or two 2 KiB steps); what is still open after that
-// goes to the whole CTA and, if longer still, to the job slots
-// (long_slide).  The few bytes the words showed equal are compared again.
-__device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S, const Pair Q, const int32_t *prev,
-                                             int32_t *cur, int64_t off, int64_t tau, int64_t a, int64_t b, int n1)
+// The open slides listed in Ld/Lc (diagonal, start row) for the frontier fr:
+// one warp each, up to t2_cap bytes (warps w0, w0 + ws, ...); the final row
+// goes to fr and the entry's diagonal becomes INT32_MIN.  Entries still open
+// are left for cta_slides.
+__device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int32_t *fr, int64_t off, int32_t *Ld,
+                                            const int32_t *Lc, int nl, int64_t a, int64_t b, int w0, int ws,
+                                            Counters &C)
 {
-    Counters C; // this call's counts, added by the caller
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    {
-        for (int j = warp; j < n1; j += nw) {
-            const int64_t d = S.ld[j];
-            const bool own = d >= a && d < b;
-            int64_t c = 0, lim = 0;
-            if (lane == 0) {
-                open_bounds(P, Q, prev, off, tau, d, &c, &lim, C, own);
-                C.opens += own;
-            }
-            c = __shfl_sync(0xffffffffu, c, 0);
-            lim = __shfl_sync(0xffffffffu, lim, 0);
-            bool open;
-            const int64_t l = slide_warp(Q.A, Q.n, Q.B, Q.m, c, c + d, 0, lim - c, P.t2_cap, &open);
-            if (!open && l >= PREFETCH_MIN) // a long slide: the next round starts past it
-                prefetch_next(Q.A, Q.n, Q.B, Q.m, c + l, c + l + d);
-            if (lane == 0) {
-                if (!open) {
-                    cur[d - off] = (int32_t)finish_slide(Q, c, d, c + l, lim, own, C);
-                    S.ld[j] = INT32_MIN; // finished
-                }
-            }
+    const int lane = threadIdx.x & 31;
+    for (int j = w0; j < nl; j += ws) {
+        const int64_t d = Ld[j], c = Lc[j];
+        const bool own = d >= a && d < b;
+        int64_t lim = 0;
+        if (lane == 0) {
+            lim = open_limit(P, Q, c, d, C, own);
+            C.opens += own;
         }
-        __syncthreads();
+        lim = __shfl_sync(0xffffffffu, lim, 0);
+        bool open;
+        const int64_t l = slide_warp(Q.A, Q.n, Q.B, Q.m, c, c + d, 0, lim - c, P.t2_cap, &open);
+        if (!open && l >= PREFETCH_MIN) // a long slide: the next round starts past it
+            prefetch_next(Q.A, Q.n, Q.B, Q.m, c + l, c + l + d);
+        if (lane == 0 && !open) {
+            fr[d - off] = (int32_t)finish_slide(Q, c, d, c + l, lim, own, C);
+            Ld[j] = INT32_MIN; // finished
+        }
     }
-    for (int j = 0; j < n1; j++) {
-        const int64_t d = S.ld[j];
+}
+
+// The listed slides a warp left open: the whole CTA each (and beyond 256
+// KiB the job slots).  Every thread must call it, after a barrier.
+__device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const Pair &Q, int32_t *fr, int64_t off,
+                                           const int32_t *Ld, const int32_t *Lc, int nl, int64_t a, int64_t b,
+                                           Counters &C)
+{
+    const int tid = threadIdx.x;
+    for (int j = 0; j < nl; j++) {
+        const int64_t d = Ld[j];
         if (d == INT32_MIN)
             continue;
+        const int64_t c = Lc[j];
         const bool own = d >= a && d < b;
-        if (tid == 0) {
-            int64_t c, lim;
-            open_bounds(P, Q, prev, off, tau, d, &c, &lim, C, own);
-            S.bcl[2] = c;
-            S.bcl[3] = lim;
-        }
+        if (tid == 0)
+            S.bcl[3] = open_limit(P, Q, c, d, C, false);
         __syncthreads();
-        const int64_t c = S.bcl[2], lim = S.bcl[3];
+        const int64_t lim = S.bcl[3];
         __syncthreads();
         const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c);
         if (lim - c > (int64_t)LOCAL_STEPS * CHUNK_BYTES && rr >= (int64_t)LOCAL_STEPS * CHUNK_BYTES)
@@ -586,10 +600,8 @@ __device__ __forceinline__ SlideCounts open_slides(const LvArgs &P, const Smem S
         if (tid < 32)
             prefetch_next(Q.A, Q.n, Q.B, Q.m, c + rr, c + rr + d);
         if (tid == 0)
-            cur[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
+            fr[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
     }
-    __syncthreads();
-    return SlideCounts{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens};
 }
 
 // What one block of rounds adds to the counters, and whether it found k.
@@ -598,78 +610,156 @@ struct BlockOut {
     int fin;
 };
 
-// Rounds t .. t+h-1 on the tile [a, b) and its shrinking halo trapezoid.
+// The round arguments of round tau on the tile [a, b) with smem offset off.
+__device__ __forceinline__ RoundArgs round_args(const LvArgs &P, const Smem S, const Pair &Q, int64_t tau,
+                                                int64_t lo, int64_t hi, int64_t off, int64_t a, int64_t b)
+{
+    RoundArgs RA;
+    RA.A = Q.A;
+    RA.B = Q.B;
+    RA.n = Q.n;
+    RA.m = Q.m;
+    RA.prev = frontier(S, tau - 1);
+    RA.cur = frontier(S, tau);
+    RA.off = off;
+    RA.lo = lo;
+    RA.hi = hi;
+    RA.tau = tau;
+    RA.a = a;
+    RA.b = b;
+    RA.err = &P.ctl->error;
+    RA.diag = P.ctl->diag;
+    RA.n1 = S.nL + (tau & 1);
+    RA.open = (tau & 1) ? S.Ld1 : S.Ld0;
+    RA.open_c = (tau & 1) ? S.Lc1 : S.Lc0;
+    RA.ocap = OCAP;
+    RA.defer = S.D;
+    RA.nd = S.nD;
+    RA.list = nullptr;
+    RA.nlist = 0;
+    RA.tid = threadIdx.x;
+    RA.nt = blockDim.x;
+    return RA;
+}
+
+// Rounds t .. t+h-1 on the tile [a, b) and its shrinking halo trapezoid,
+// pipelined: while warps 0..W-2 compute round tau for every diagonal whose
+// predecessors are final, the last warp finishes the open slides of round
+// tau - 1 (the path's slide of about n/k bytes, every round); the diagonals
+// next to those slides are deferred and computed once they are final.  A
+// listed slide a warp cannot finish goes to the whole CTA.  The last round's
+// open slides are finished by all warps before the block ends (its edges go
+// to the neighbours).  Round tau - 1 is final after round tau's slide phase:
+// the termination test and the frontier dump see only final rows.
 __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, const Pair Q, int32_t *dump,
                                           int32_t dump_tmax, unsigned long long *res, GroupCtl *gc, int64_t t,
                                           int h, int64_t a, int64_t b)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
+    const bool slider = warp == nw - 1;
     const int64_t n = Q.n, m = Q.m, target = m - n;
     const int64_t off = a - h - 1; // smem index = d - off
     Counters C;
-    bool fin = false;
-    for (int r = 0; r < h && !fin; r++) {
+    int64_t kfound = -1;
+    // is row tau of the target diagonal n?  (tau's band holds it and it is this tile's)
+    auto hit = [=](int64_t tau) {
+        const int64_t blo = max(-tau, -n), bhi = min(tau, m);
+        return target >= a && target < b && target >= blo && target <= bhi &&
+               frontier(S, tau)[target - off] == n;
+    };
+    auto dump_row = [=](int64_t tau) {
+        if (dump && tau <= dump_tmax) {
+            const int64_t TT = dump_tmax;
+            const int32_t *fr = frontier(S, tau);
+            for (int64_t d = max(a, -TT) + tid; d < min(b, TT + 1); d += nt)
+                dump[tau * (2 * TT + 1) + d + TT] = fr[d - off];
+        }
+    };
+    if (tid == 0) {
+        S.nL[0] = S.nL[1] = 0;
+        *S.nD = 0;
+    }
+    __syncthreads();
+    int r = 0;
+    for (; r < h && kfound < 0; r++) {
         const uint64_t tr0 = clock64();
         const int64_t tau = t + r;
         const int64_t ra = a - h + 1 + r, rb = b + h - 1 - r; // computed range [ra, rb)
         const int64_t blo = max(-tau, -n), bhi = min(tau, m);
         int32_t *cur = frontier(S, tau);
+        int32_t *prev = frontier(S, tau - 1);
         // outside the band: minus infinity
         for (int64_t d = ra + tid; d < rb; d += nt)
             if (d < blo || d > bhi)
                 cur[d - off] = NEG;
-        RoundArgs RA;
-        RA.A = Q.A;
-        RA.B = Q.B;
-        RA.n = n;
-        RA.m = m;
-        RA.prev = frontier(S, tau - 1);
-        RA.cur = cur;
-        RA.off = off;
-        RA.lo = max(ra, blo);
-        RA.hi = min(rb - 1, bhi);
-        RA.tau = tau;
-        RA.a = a;
-        RA.b = b;
-        RA.n1 = S.n1;
-        RA.open = S.ld;
-        RA.err = &P.ctl->error;
-        RA.diag = P.ctl->diag;
-        const RoundCount rc = tile_round<2048 / CTA_THREADS>(RA);
-        C.slide += rc.slide;
-        C.mism += rc.mism;
+        const int pp = (int)((tau - 1) & 1);
+        int32_t *Ldp = pp ? S.Ld1 : S.Ld0;
+        const int32_t *Lcp = pp ? S.Lc1 : S.Lc0;
+        const int nlp = r > 0 ? min(S.nL[pp], OCAP) : 0;
+        // -------- phase 1: the slides of round tau - 1 || round tau
+        if (slider) {
+            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, 0, 1, C);
+        } else {
+            RoundArgs RA = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
+            RA.nt = nt - 32;
+            const RoundCount rc = tile_round<2048 / CTA_THREADS, true>(RA);
+            C.slide += rc.slide;
+            C.mism += rc.mism;
+        }
         __syncthreads();
-        const uint64_t tr1 = clock64();
-        C.tm[0] += tr1 - tr0;
-        const int n1 = *S.n1;
-        if (n1 > 0) {
-            const SlideCounts oc = open_slides(P, S, Q, frontier(S, tau - 1), cur, off, tau, a, b, n1);
-            C.slide += oc.slide;
-            C.mism += oc.mism;
-            C.hashq += oc.hashq;
-            C.coll += oc.coll;
-            C.longs += oc.longs;
-            C.opens += oc.opens;
-            if (tid == 0)
-                *S.n1 = 0;
-            C.tm[1] += clock64() - tr1;
+        // -------- phase 2: slides the warp left open, then the deferred diagonals
+        if (nlp > 0)
+            cta_slides(P, S, Q, prev, off, Ldp, Lcp, nlp, a, b, C);
+        const int nd = *S.nD;
+        if (nd > 0) {
+            RoundArgs RA = round_args(P, S, Q, tau, 0, -1, off, a, b);
+            RA.list = S.D;
+            RA.nlist = nd;
+            const RoundCount rc = tile_round<1, true, true>(RA);
+            C.slide += rc.slide;
+            C.mism += rc.mism;
         }
-        // termination: the tile owning the target diagonal reports k
-        if (target >= a && target < b && target >= blo && target <= bhi && cur[target - off] == n) {
-            fin = true;
-            if (tid == 0) {
-                atomicMin(&gc->done_k, (unsigned long long)tau);
-                res[R_K] = (unsigned long long)tau;
-            }
+        __syncthreads();
+        // round tau - 1 is final now; round tau wherever it is not PENDING
+        if (r > 0) {
+            dump_row(tau - 1);
+            if (hit(tau - 1))
+                kfound = tau - 1;
         }
-        if (dump && tau <= dump_tmax) {
-            const int64_t TT = dump_tmax;
-            for (int64_t d = max(a, -TT) + tid; d < min(b, TT + 1); d += nt)
-                dump[tau * (2 * TT + 1) + d + TT] = cur[d - off];
+        if (kfound < 0 && hit(tau))
+            kfound = tau;
+        if (tid == 0) {
+            S.nL[pp] = 0; // consumed
+            *S.nD = 0;
         }
+        C.tm[0] += clock64() - tr0;
         __syncthreads();
     }
-    return BlockOut{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens, C.tm[0], C.tm[1], fin ? 1 : 0};
+    // -------- the last computed round's open slides: all warps
+    const uint64_t to0 = clock64();
+    const int64_t tl = t + r - 1;
+    if (kfound < 0 || kfound == tl) {
+        const int pl = (int)(tl & 1);
+        int32_t *Ldl = pl ? S.Ld1 : S.Ld0;
+        const int32_t *Lcl = pl ? S.Lc1 : S.Lc0;
+        const int nll = min(S.nL[pl], OCAP);
+        if (nll > 0) {
+            warp_slides(P, Q, frontier(S, tl), off, Ldl, Lcl, nll, a, b, warp, nw, C);
+            __syncthreads();
+            cta_slides(P, S, Q, frontier(S, tl), off, Ldl, Lcl, nll, a, b, C);
+            __syncthreads();
+        }
+        dump_row(tl);
+        if (kfound < 0 && hit(tl))
+            kfound = tl;
+    }
+    C.tm[1] += clock64() - to0;
+    if (kfound >= 0 && tid == 0) {
+        atomicMin(&gc->done_k, (unsigned long long)kfound);
+        res[R_K] = (unsigned long long)kfound;
+    }
+    __syncthreads();
+    return BlockOut{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens, C.tm[0], C.tm[1], kfound >= 0 ? 1 : 0};
 }
 
 // Whether a CTA that is about to compute round t leaves the pair.  Once k
