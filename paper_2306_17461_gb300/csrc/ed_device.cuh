@@ -356,7 +356,7 @@ __device__ __forceinline__ int64_t cta_scan(const uint8_t *A, int64_t n, const u
         *s_min = ~0ull;
     __syncthreads();
     int64_t best = -1;
-    for (int64_t base = 0; base < len && best < 0; base += (int64_t)nt * 16 * UNROLL) {
+    for (int64_t base = 0; base < len; base += (int64_t)nt * 16 * UNROLL) {
         // every aligned block first (windows past len read a valid block and
         // are ignored below), then the compares
         uint4 alo[UNROLL], ahi[UNROLL], blo[UNROLL], bhi[UNROLL];
@@ -381,6 +381,9 @@ __device__ __forceinline__ int64_t cta_scan(const uint8_t *A, int64_t n, const u
                     best = off + o + f;
             }
         }
+        // the whole CTA stops after the first step with a mismatch
+        if (__syncthreads_or(best >= 0))
+            break;
     }
     if (best >= 0)
         atomicMin(s_min, (unsigned long long)best);

@@ -11,9 +11,10 @@
 //
 // GB300 mapping.
 //  * The CTAs of a group split the diagonals of [-R, R] into static tiles,
-//    one per CTA, each kept in shared memory.  R (the epoch radius) doubles
-//    when the band [-t, t] reaches it; tiles are then re-cut through a
-//    global buffer behind a group barrier (O(log k) times in all).
+//    one per CTA, each kept in shared memory.  R (the epoch radius) grows
+//    by a quarter when the band [-t, t] reaches it; tiles are then re-cut
+//    through a global buffer behind a group barrier (O(log k) times in all).
+//    The busiest tiles are then at most 1.25 times the band's share.
 //  * Temporal blocking: a CTA holds its tile plus h diagonals of halo on
 //    each side and runs h rounds on the shrinking trapezoid (the halo
 //    diagonals are recomputed, exactly), then trades its h edge values with
@@ -40,6 +41,7 @@
 namespace edg {
 
 constexpr int LOCAL_STEPS = 4;            // 64 KiB steps the owner takes alone
+constexpr int64_t GROW_NUM = 5, GROW_DEN = 4; // epoch radius growth factor
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
 struct Counters {
@@ -210,7 +212,9 @@ struct Smem {
     // pipelined rounds: open lists by round parity (diagonal, start row;
     // OCAP entries each) and their counts, the deferred diagonals of a round
     int32_t *Ld0, *Ld1, *Lc0, *Lc1, *D;
-    int *nL, *nD;
+    int *nL, *nD;       // by round parity
+    int *left;          // the slider warp left a listed slide open
+    int *kf;            // the target diagonal reached row n in the round before
     int *n1;
     int *bc;            // 8 broadcast words
     long long *bcl;     // 4 broadcast 64-bit words
@@ -484,6 +488,8 @@ __device__ Smem carve(const LvArgs &P)
     S.bc = S.n1 + 4;
     S.nL = reinterpret_cast<int *>(p + 128);
     S.nD = S.nL + 2;
+    S.left = S.nL + 4;
+    S.kf = S.nL + 5;
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -553,7 +559,7 @@ __device__ __forceinline__ int64_t open_limit(const LvArgs &P, const Pair &Q, in
 // are left for cta_slides.
 __device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int32_t *fr, int64_t off, int32_t *Ld,
                                             const int32_t *Lc, int nl, int64_t a, int64_t b, int w0, int ws,
-                                            Counters &C)
+                                            Counters &C, int *left)
 {
     const int lane = threadIdx.x & 31;
     for (int j = w0; j < nl; j += ws) {
@@ -573,20 +579,25 @@ __device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int3
             fr[d - off] = (int32_t)finish_slide(Q, c, d, c + l, lim, own, C);
             Ld[j] = INT32_MIN; // finished
         }
+        if (lane == 0 && open && left)
+            *left = 1;
     }
 }
 
 // The listed slides a warp left open: the whole CTA each (and beyond 256
-// KiB the job slots).  Every thread must call it, after a barrier.
+// KiB the job slots).  Every thread must call it, after a barrier; the
+// final rows are visible to every thread when it returns.
 __device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const Pair &Q, int32_t *fr, int64_t off,
                                            const int32_t *Ld, const int32_t *Lc, int nl, int64_t a, int64_t b,
                                            Counters &C)
 {
     const int tid = threadIdx.x;
+    bool any = false;
     for (int j = 0; j < nl; j++) {
         const int64_t d = Ld[j];
         if (d == INT32_MIN)
             continue;
+        any = true;
         const int64_t c = Lc[j];
         const bool own = d >= a && d < b;
         if (tid == 0)
@@ -602,6 +613,8 @@ __device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const 
         if (tid == 0)
             fr[d - off] = (int32_t)finish_slide(Q, c, d, c + rr, lim, own, C);
     }
+    if (any) // (every thread saw the same entries)
+        __syncthreads();
 }
 
 // What one block of rounds adds to the counters, and whether it found k.
@@ -634,7 +647,7 @@ __device__ __forceinline__ RoundArgs round_args(const LvArgs &P, const Smem S, c
     RA.open_c = (tau & 1) ? S.Lc1 : S.Lc0;
     RA.ocap = OCAP;
     RA.defer = S.D;
-    RA.nd = S.nD;
+    RA.nd = S.nD + (tau & 1);
     RA.list = nullptr;
     RA.nlist = 0;
     RA.tid = threadIdx.x;
@@ -650,7 +663,10 @@ __device__ __forceinline__ RoundArgs round_args(const LvArgs &P, const Smem S, c
 // listed slide a warp cannot finish goes to the whole CTA.  The last round's
 // open slides are finished by all warps before the block ends (its edges go
 // to the neighbours).  Round tau - 1 is final after round tau's slide phase:
-// the termination test and the frontier dump see only final rows.
+// the termination test and the frontier dump see only final rows.  Two
+// barriers a round (three with a frontier dump): the open and deferred
+// counts alternate by round parity, and thread 0 tests round tau - 1 for
+// termination before the second.
 __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, const Pair Q, int32_t *dump,
                                           int32_t dump_tmax, unsigned long long *res, GroupCtl *gc, int64_t t,
                                           int h, int64_t a, int64_t b)
@@ -677,7 +693,8 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
     };
     if (tid == 0) {
         S.nL[0] = S.nL[1] = 0;
-        *S.nD = 0;
+        S.nD[0] = S.nD[1] = 0;
+        *S.left = 0;
     }
     __syncthreads();
     int r = 0;
@@ -688,17 +705,21 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         const int64_t blo = max(-tau, -n), bhi = min(tau, m);
         int32_t *cur = frontier(S, tau);
         int32_t *prev = frontier(S, tau - 1);
-        // outside the band: minus infinity
-        for (int64_t d = ra + tid; d < rb; d += nt)
-            if (d < blo || d > bhi)
-                cur[d - off] = NEG;
+        // outside the band (past either of its ends): minus infinity
+        for (int64_t d = ra + tid; d < min(rb, blo); d += nt)
+            cur[d - off] = NEG;
+        for (int64_t d = max(ra, bhi + 1) + tid; d < rb; d += nt)
+            cur[d - off] = NEG;
         const int pp = (int)((tau - 1) & 1);
         int32_t *Ldp = pp ? S.Ld1 : S.Ld0;
         const int32_t *Lcp = pp ? S.Lc1 : S.Lc0;
         const int nlp = r > 0 ? min(S.nL[pp], OCAP) : 0;
         // -------- phase 1: the slides of round tau - 1 || round tau
         if (slider) {
-            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, 0, 1, C);
+            if (tid == nt - 32)
+                *S.left = 0; // read by every thread before the last barrier of round tau - 1
+            __syncwarp();
+            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, 0, 1, C, S.left);
         } else {
             RoundArgs RA = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
             RA.nt = nt - 32;
@@ -708,9 +729,20 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         }
         __syncthreads();
         // -------- phase 2: slides the warp left open, then the deferred diagonals
-        if (nlp > 0)
+        if (nlp > 0 && *S.left)
             cta_slides(P, S, Q, prev, off, Ldp, Lcp, nlp, a, b, C);
-        const int nd = *S.nD;
+        const int nd = S.nD[tau & 1];
+        if (tid == 0) {
+            // round tau - 1's list is consumed (every thread read its count
+            // before the first barrier); the same parity's counts serve round
+            // tau + 1 (round tau - 1's deferred count was last read before
+            // the second barrier of round tau - 1)
+            S.nL[pp] = 0;
+            S.nD[pp] = 0;
+            // round tau - 1 is final here for thread 0: the slider's rows
+            // before the first barrier, the CTA's slides by thread 0 itself
+            *S.kf = r > 0 && hit(tau - 1);
+        }
         if (nd > 0) {
             RoundArgs RA = round_args(P, S, Q, tau, 0, -1, off, a, b);
             RA.list = S.D;
@@ -720,20 +752,17 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
             C.mism += rc.mism;
         }
         __syncthreads();
-        // round tau - 1 is final now; round tau wherever it is not PENDING
-        if (r > 0) {
-            dump_row(tau - 1);
-            if (hit(tau - 1))
-                kfound = tau - 1;
-        }
-        if (kfound < 0 && hit(tau))
-            kfound = tau;
-        if (tid == 0) {
-            S.nL[pp] = 0; // consumed
-            *S.nD = 0;
+        // round tau - 1 is final now (round tau is tested in the next round,
+        // or below if tau ends the block)
+        if (*S.kf)
+            kfound = tau - 1;
+        if (dump) {
+            // round tau + 1 overwrites this buffer
+            if (r > 0)
+                dump_row(tau - 1);
+            __syncthreads();
         }
         C.tm[0] += clock64() - tr0;
-        __syncthreads();
     }
     // -------- the last computed round's open slides: all warps
     const uint64_t to0 = clock64();
@@ -744,7 +773,7 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         const int32_t *Lcl = pl ? S.Lc1 : S.Lc0;
         const int nll = min(S.nL[pl], OCAP);
         if (nll > 0) {
-            warp_slides(P, Q, frontier(S, tl), off, Ldl, Lcl, nll, a, b, warp, nw, C);
+            warp_slides(P, Q, frontier(S, tl), off, Ldl, Lcl, nll, a, b, warp, nw, C, nullptr);
             __syncthreads();
             cta_slides(P, S, Q, frontier(S, tl), off, Ldl, Lcl, nll, a, b, C);
             __syncthreads();
@@ -920,7 +949,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             int64_t Rn = R;
             bool wide = false; // the band outgrew the tiles: save it for wider ones
             if (grow) {
-                Rn = min(max(2 * R, t + h - 1), min(nm, (int64_t)P.kcap));
+                Rn = min(max(R * GROW_NUM / GROW_DEN, t + h - 1), min(nm, (int64_t)P.kcap));
                 if (t + h - 1 > Rn && Rn < nm) {
                     pair_stop(D, gc, ST_LIMIT);
                     return true;
