@@ -12,9 +12,9 @@
 // GB300 mapping.
 //  * The CTAs of a group split the diagonals of [-R, R] into static tiles,
 //    one per CTA, each kept in shared memory.  R (the epoch radius) grows
-//    by a quarter when the band [-t, t] reaches it; tiles are then re-cut
+//    by an eighth when the band [-t, t] reaches it; tiles are then re-cut
 //    through a global buffer behind a group barrier (O(log k) times in all).
-//    The busiest tiles are then at most 1.25 times the band's share.
+//    The busiest tiles are then at most 1.125 times the band's share.
 //  * Temporal blocking: a CTA holds its tile plus h diagonals of halo on
 //    each side and runs h rounds on the shrinking trapezoid (the halo
 //    diagonals are recomputed, exactly), then trades its h edge values with
@@ -41,7 +41,7 @@
 namespace edg {
 
 constexpr int LOCAL_STEPS = 4;            // 64 KiB steps the owner takes alone
-constexpr int64_t GROW_NUM = 5, GROW_DEN = 4; // epoch radius growth factor
+constexpr int64_t GROW_NUM = 9, GROW_DEN = 8; // epoch radius growth factor
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
 struct Counters {
@@ -213,7 +213,7 @@ struct Smem {
     // OCAP entries each) and their counts, the deferred diagonals of a round
     int32_t *Ld0, *Ld1, *Lc0, *Lc1, *D;
     int *nL, *nD;       // by round parity
-    int *left;          // the slider warp left a listed slide open
+    int *left;          // a slider warp left a listed slide open (by round parity)
     int *kf;            // the target diagonal reached row n in the round before
     int *n1;
     int *bc;            // 8 broadcast words
@@ -489,7 +489,7 @@ __device__ Smem carve(const LvArgs &P)
     S.nL = reinterpret_cast<int *>(p + 128);
     S.nD = S.nL + 2;
     S.left = S.nL + 4;
-    S.kf = S.nL + 5;
+    S.kf = S.nL + 6;
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -656,9 +656,10 @@ __device__ __forceinline__ RoundArgs round_args(const LvArgs &P, const Smem S, c
 }
 
 // Rounds t .. t+h-1 on the tile [a, b) and its shrinking halo trapezoid,
-// pipelined: while warps 0..W-2 compute round tau for every diagonal whose
-// predecessors are final, the last warp finishes the open slides of round
-// tau - 1 (the path's slide of about n/k bytes, every round); the diagonals
+// pipelined: while six warps compute round tau for every diagonal whose
+// predecessors are final, warps 3 and 7 finish the open slides of round
+// tau - 1 (the path's slide of about n/k bytes, every round, and the
+// chance matches beside it, in parallel); the diagonals
 // next to those slides are deferred and computed once they are final.  A
 // listed slide a warp cannot finish goes to the whole CTA.  The last round's
 // open slides are finished by all warps before the block ends (its edges go
@@ -672,7 +673,10 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
                                           int h, int64_t a, int64_t b)
 {
     const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, nw = nt >> 5;
-    const bool slider = warp == nw - 1;
+    // the slider warps are the last of each group of four (warps 3 and 7);
+    // the other six compute the round
+    const bool slider = (warp & 3) == 3;
+    const int nsl = nw / 4, sli = warp >> 2;
     const int64_t n = Q.n, m = Q.m, target = m - n;
     const int64_t off = a - h - 1; // smem index = d - off
     Counters C;
@@ -694,7 +698,7 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
     if (tid == 0) {
         S.nL[0] = S.nL[1] = 0;
         S.nD[0] = S.nD[1] = 0;
-        *S.left = 0;
+        S.left[0] = S.left[1] = 0;
     }
     __syncthreads();
     int r = 0;
@@ -716,20 +720,18 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         const int nlp = r > 0 ? min(S.nL[pp], OCAP) : 0;
         // -------- phase 1: the slides of round tau - 1 || round tau
         if (slider) {
-            if (tid == nt - 32)
-                *S.left = 0; // read by every thread before the last barrier of round tau - 1
-            __syncwarp();
-            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, 0, 1, C, S.left);
+            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, sli, nsl, C, S.left + (tau & 1));
         } else {
             RoundArgs RA = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
-            RA.nt = nt - 32;
+            RA.tid = tid - 32 * sli;
+            RA.nt = nt - 32 * nsl;
             const RoundCount rc = tile_round<2048 / CTA_THREADS, true>(RA);
             C.slide += rc.slide;
             C.mism += rc.mism;
         }
         __syncthreads();
         // -------- phase 2: slides the warp left open, then the deferred diagonals
-        if (nlp > 0 && *S.left)
+        if (nlp > 0 && S.left[tau & 1])
             cta_slides(P, S, Q, prev, off, Ldp, Lcp, nlp, a, b, C);
         const int nd = S.nD[tau & 1];
         if (tid == 0) {
@@ -739,6 +741,7 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
             // the second barrier of round tau - 1)
             S.nL[pp] = 0;
             S.nD[pp] = 0;
+            S.left[pp] = 0;
             // round tau - 1 is final here for thread 0: the slider's rows
             // before the first barrier, the CTA's slides by thread 0 itself
             *S.kf = r > 0 && hit(tau - 1);
