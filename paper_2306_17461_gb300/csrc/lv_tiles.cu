@@ -215,6 +215,7 @@ struct Smem {
     int *nL, *nD;       // by round parity
     int *left;          // a slider warp left a listed slide open (by round parity)
     int *kf;            // the target diagonal reached row n in the round before
+    int *nR;            // deferred diagonals a slider warp computed (by round parity)
     int *n1;
     int *bc;            // 8 broadcast words
     long long *bcl;     // 4 broadcast 64-bit words
@@ -490,6 +491,7 @@ __device__ Smem carve(const LvArgs &P)
     S.nD = S.nL + 2;
     S.left = S.nL + 4;
     S.kf = S.nL + 6;
+    S.nR = S.nL + 7;
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -557,9 +559,15 @@ __device__ __forceinline__ int64_t open_limit(const LvArgs &P, const Pair &Q, in
 // one warp each, up to t2_cap bytes (warps w0, w0 + ws, ...); the final row
 // goes to fr and the entry's diagonal becomes INT32_MIN.  Entries still open
 // are left for cta_slides.
+//
+// nb (pipelined rounds): round tau, whose diagonals next to a slide of
+// round tau - 1 wait for it (DEFER_MARK).  Once a slide is done, lanes 0..2
+// claim its three neighbours in round tau and compute them (the bytes at
+// the slide's end are in L1), unless another predecessor is still open;
+// *nr counts those computed.
 __device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int32_t *fr, int64_t off, int32_t *Ld,
                                             const int32_t *Lc, int nl, int64_t a, int64_t b, int w0, int ws,
-                                            Counters &C, int *left)
+                                            Counters &C, int *left, const RoundArgs *nb = nullptr, int *nr = nullptr)
 {
     const int lane = threadIdx.x & 31;
     for (int j = w0; j < nl; j += ws) {
@@ -581,6 +589,24 @@ __device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int3
         }
         if (lane == 0 && open && left)
             *left = 1;
+        if (nb && !open) {
+            __syncwarp(); // the final row, written by lane 0
+            const int32_t e = (int32_t)d - 1 + lane;
+            if (lane < 3 && e >= nb->lo && e <= nb->hi) {
+                int32_t *cp = nb->cur + (e - nb->off);
+                if (atomicCAS(cp, DEFER_MARK, DEFER_CLAIM) == DEFER_MARK) {
+                    RoundCount rc = {0, 0};
+                    if (round_one(*nb, e, rc)) {
+                        C.slide += rc.slide;
+                        C.mism += rc.mism;
+                        atomicAdd(nr, 1);
+                    } else {
+                        atomicExch(cp, DEFER_MARK); // the deferred pass takes it
+                    }
+                }
+            }
+            __syncwarp();
+        }
     }
 }
 
@@ -699,6 +725,7 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         S.nL[0] = S.nL[1] = 0;
         S.nD[0] = S.nD[1] = 0;
         S.left[0] = S.left[1] = 0;
+        S.nR[0] = S.nR[1] = 0;
     }
     __syncthreads();
     int r = 0;
@@ -720,7 +747,9 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         const int nlp = r > 0 ? min(S.nL[pp], OCAP) : 0;
         // -------- phase 1: the slides of round tau - 1 || round tau
         if (slider) {
-            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, sli, nsl, C, S.left + (tau & 1));
+            const RoundArgs RN = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
+            warp_slides(P, Q, prev, off, Ldp, Lcp, nlp, a, b, sli, nsl, C, S.left + (tau & 1), &RN,
+                        S.nR + (tau & 1));
         } else {
             RoundArgs RA = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
             RA.tid = tid - 32 * sli;
@@ -733,7 +762,8 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
         // -------- phase 2: slides the warp left open, then the deferred diagonals
         if (nlp > 0 && S.left[tau & 1])
             cta_slides(P, S, Q, prev, off, Ldp, Lcp, nlp, a, b, C);
-        const int nd = S.nD[tau & 1];
+        const int nd = S.nD[tau & 1];                   // deferred diagonals listed
+        const bool marked = nd > S.nR[tau & 1];          // not all computed by a slider warp
         if (tid == 0) {
             // round tau - 1's list is consumed (every thread read its count
             // before the first barrier); the same parity's counts serve round
@@ -742,11 +772,12 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
             S.nL[pp] = 0;
             S.nD[pp] = 0;
             S.left[pp] = 0;
+            S.nR[pp] = 0;
             // round tau - 1 is final here for thread 0: the slider's rows
             // before the first barrier, the CTA's slides by thread 0 itself
             *S.kf = r > 0 && hit(tau - 1);
         }
-        if (nd > 0) {
+        if (marked) {
             RoundArgs RA = round_args(P, S, Q, tau, 0, -1, off, a, b);
             RA.list = S.D;
             RA.nlist = nd;
