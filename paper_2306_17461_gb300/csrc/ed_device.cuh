@@ -1,12 +1,12 @@
 // ed_device.cuh -- device building blocks shared by the GB300 kernels.
 //
-// Notation (spec convention, mirrored from the paper's i = x - y):
+// Notation (the paper's diagonal i = x - y, mirrored):
 //   cell (x, y) = x bytes of A and y bytes of B consumed; diagonal d = y - x;
 //   L_t[d] = furthest row x on diagonal d reachable with t edits.
 // LCP(x, y) (Sec. 2) = length of the longest common prefix of A[x..n) and
 // B[y..m).  The slides below compute it by direct comparison in 16-byte
-// windows (the paper's "compare the leading characters first", Sec. 5.1,
-// widened to a 16-byte vector compare).
+// windows (Sec. 5.1 checks a few leading characters before a query; here
+// that check is a 16-byte vector compare).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
