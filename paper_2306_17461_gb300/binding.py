@@ -87,6 +87,7 @@ _SIGS = {
     "ed_prefix_hash_blocked_dev": (_I, [_P, _P, _S, _S, _P, _P]),
     "ed_hash_base": (_U64, [_P]),
     "ed_frontiers_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _P, _P]),
+    "ed_edit_script_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _S, _P, _P, _P]),
     "ed_prefix_hash_noalloc": (_I, [_P, _S, _U64, _P, _P]),
 }
 
@@ -331,6 +332,22 @@ def ed_frontiers_dev(ctx, A, B, t_max: int, stream=None):
                                         _stream_ptr(stream)), "ed_frontiers_dev")
     kk = int(k.value)
     return (None if kk == 2**64 - 1 else kk), F
+
+
+ED_OP_SUB, ED_OP_DEL, ED_OP_INS = 0, 1, 2
+
+
+def ed_edit_script_dev(ctx, A, B, t_max: int, stream=None):
+    """(k, ops) with ops an (k, 3) int64 array of (kind, x, y): an optimal
+    edit script of A into B, in order from the start of the strings."""
+    pa, n = _dev_buf(A)
+    pb, m = _dev_buf(B)
+    ops = np.zeros((max(t_max, 1), 3), dtype=np.int64)
+    nops = ctypes.c_size_t()
+    k = ctypes.c_uint64()
+    _check(ctx, load().ed_edit_script_dev(ctx, pa, n, pb, m, t_max, ops.ctypes.data, t_max, ctypes.byref(nops),
+                                          ctypes.byref(k), _stream_ptr(stream)), "ed_edit_script_dev")
+    return int(k.value), ops[: int(nops.value)].copy()
 
 
 class Context:

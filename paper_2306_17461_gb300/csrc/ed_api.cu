@@ -779,6 +779,94 @@ int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, 
     return ED_OK;
 }
 
+// The walk back of ed_edit_script_dev over the frontiers F (rows 0..k of
+// a dump with bound T).  ops receives (kind, x, y) triples from the end of
+// the strings backwards.  Returns false if the frontiers contradict
+// themselves (a device error).
+static bool trace_script(const int32_t *F, int64_t T, int64_t n, int64_t m, int64_t k, std::vector<int64_t> &ops)
+{
+    constexpr int64_t NONE = INT64_MIN;
+    const int64_t W = 2 * T + 1;
+    auto L = [&](int64_t t, int64_t d) -> int64_t {
+        if (t < 0 || d < -t || d > t)
+            return NONE;
+        const int32_t v = F[t * W + d + T];
+        return v < 0 ? NONE : (int64_t)v;
+    };
+    int64_t x = n, y = m, t = k;
+    while (x > 0 || y > 0) {
+        const int64_t d = y - x;
+        if (t == 0) // the slide of round 0 from (0, 0)
+            return d == 0 && x <= L(0, 0);
+        const int64_t a1 = L(t - 1, d - 1), a2 = L(t - 1, d), a3 = L(t - 1, d + 1);
+        if (a2 != NONE && x <= a2) { // distance at most t - 1 already
+            t--;
+            continue;
+        }
+        // the start row of round t's slide on diagonal d
+        int64_t c = NONE;
+        if (a1 != NONE)
+            c = std::max(c, a1);
+        if (a2 != NONE)
+            c = std::max(c, a2 + 1);
+        if (a3 != NONE)
+            c = std::max(c, a3 + 1);
+        if (c == NONE)
+            return false;
+        c = std::min(c, d <= m - n ? n : m - d);
+        if (x > c) { // back along the slide: matches
+            x = c;
+            y = c + d;
+            continue;
+        }
+        if (x < c)
+            return false;
+        // one edit from a cell of distance t - 1
+        if (x >= 1 && y >= 1 && a2 != NONE && x - 1 <= a2) {
+            ops.insert(ops.end(), {(int64_t)ED_OP_SUB, x - 1, y - 1});
+            x--, y--;
+        } else if (x >= 1 && a3 != NONE && x - 1 <= a3) {
+            ops.insert(ops.end(), {(int64_t)ED_OP_DEL, x - 1, y});
+            x--;
+        } else if (y >= 1 && a1 != NONE && x <= a1) {
+            ops.insert(ops.end(), {(int64_t)ED_OP_INS, x, y - 1});
+            y--;
+        } else {
+            return false;
+        }
+        t--;
+    }
+    return true;
+}
+
+int ed_edit_script_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
+                       int64_t *ops, size_t cap, size_t *nops, uint64_t *k, void *stream)
+{
+    if (!ctx || !k || !nops || (cap && !ops) || t_max < 0 || t_max > 4096 || (n && !A) || (m && !B) ||
+        bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    std::vector<int32_t> F((size_t)(t_max + 1) * (size_t)(2 * t_max + 1));
+    uint64_t kk = 0;
+    int r = ed_frontiers_dev(ctx, A, n, B, m, t_max, F.data(), &kk, stream);
+    if (r != ED_OK)
+        return r;
+    *k = kk;
+    *nops = 0;
+    if (kk == UINT64_MAX)
+        return ED_ELIMIT;
+    if (cap < kk)
+        return ED_EINVAL;
+    std::vector<int64_t> back;
+    back.reserve(3 * (size_t)kk);
+    if (!trace_script(F.data(), t_max, (int64_t)n, (int64_t)m, (int64_t)kk, back) || back.size() != 3 * kk)
+        return ED_ECUDA; // frontiers that contradict themselves: a device fault
+    for (size_t i = 0; i < kk; i++)
+        for (int j = 0; j < 3; j++)
+            ops[3 * i + j] = back[3 * (kk - 1 - i) + j];
+    *nops = (size_t)kk;
+    return ED_OK;
+}
+
 int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T, void *stream)
 {
     if (!ctx || !T || (len && !X) || bad_len(len))
