@@ -40,7 +40,7 @@
 
 namespace edg {
 
-constexpr int LOCAL_STEPS = 4;            // 64 KiB steps the owner takes alone
+constexpr int LOCAL_STEPS = 2;            // 64 KiB steps the owner takes alone
 constexpr int64_t GROW_NUM = 9, GROW_DEN = 8; // epoch radius growth factor
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
@@ -610,7 +610,7 @@ __device__ __forceinline__ void warp_slides(const LvArgs &P, const Pair &Q, int3
     }
 }
 
-// The listed slides a warp left open: the whole CTA each (and beyond 256
+// The listed slides a warp left open: the whole CTA each (and beyond 128
 // KiB the job slots).  Every thread must call it, after a barrier; the
 // final rows are visible to every thread when it returns.
 __device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const Pair &Q, int32_t *fr, int64_t off,
