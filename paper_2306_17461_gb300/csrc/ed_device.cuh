@@ -259,6 +259,22 @@ static __device__ __noinline__ int64_t slide_more(const uint8_t *A, int64_t n, c
     return l;
 }
 
+// Asks L2 for len bytes of X from byte x on (clipped to the string), by the
+// copy engine: one bulk prefetch, no load issued by the calling thread.  It
+// covers whole 16-byte blocks, never past the one that holds the string's
+// last byte.
+__device__ __forceinline__ void bulk_prefetch_l2(const uint8_t *X, int64_t len_x, int64_t x, int64_t len)
+{
+    if (x < 0 || x >= len_x || len <= 0)
+        return;
+    const uintptr_t lo = (uintptr_t)(X + x) & ~(uintptr_t)15;
+    const uintptr_t end = ((uintptr_t)(X + len_x) + 15) & ~(uintptr_t)15;
+    const uintptr_t hi = min((((uintptr_t)(X + x) + (uintptr_t)len) + 15) & ~(uintptr_t)15, end);
+    uint64_t g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(lo));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(g), "r"((uint32_t)(hi - lo)) : "memory");
+}
+
 // Slides at least this long are followed by a prefetch of what follows
 // them (shorter ones are chance matches off the alignment path).
 constexpr int64_t PREFETCH_MIN = 256;

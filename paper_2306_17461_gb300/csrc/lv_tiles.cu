@@ -344,6 +344,13 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const 
                                            int64_t y, int64_t lim)
 {
     const int tid = threadIdx.x;
+    // what the CTA scans alone, asked of L2 at once: the steps below then
+    // wait on L2 rather than on DRAM
+    if (tid == 0) {
+        const int64_t ahead = min(lim, (int64_t)LOCAL_STEPS * CHUNK_BYTES);
+        bulk_prefetch_l2(Q.A, Q.n, x, ahead);
+        bulk_prefetch_l2(Q.B, Q.m, y, ahead);
+    }
     int64_t off = 0;
     for (int step = 0; step < LOCAL_STEPS && off < lim; step++) {
         const int64_t r = cta_scan<4>(Q.A, Q.n, Q.B, Q.m, x, y, off,
