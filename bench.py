@@ -153,10 +153,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the translation unit of lv_tiles_kernel: the sources its counters depend on
+TILE_KERNEL_SOURCES = ("ed_device.cuh", "lv_kernels.cuh", "lv_round.cuh", "lv_tiles.cu")
+
+
 def src_hash() -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_2306_17461_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
+    for f in TILE_KERNEL_SOURCES:
         with open(os.path.join(cs, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
