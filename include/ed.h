@@ -248,6 +248,16 @@ int ed_edit_script_dev(ed_ctx *ctx, const uint8_t *A, size_t n,
                        int64_t *ops, size_t cap, size_t *nops, uint64_t *k,
                        void *stream);
 
+/* The walk back of ed_edit_script_dev over frontiers the caller supplies:
+ * F is a HOST array F[t * (2*t_max+1) + (d + t_max)] = L_t[d] for rounds
+ * 0..k (negative where undefined: the layout ed_frontiers_dev writes) for
+ * strings of lengths n and m at distance k <= t_max.  Host work only.  ops,
+ * cap and *nops as in ed_edit_script_dev; the characters themselves are
+ * not needed.  ED_EINVAL for a null pointer, k > t_max, cap < k, or
+ * frontiers that do not describe a distance-k alignment of those lengths. */
+int ed_trace_script(const int32_t *F, int64_t t_max, size_t n, size_t m, uint64_t k,
+                    int64_t *ops, size_t cap, size_t *nops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,7 @@ _SIGS = {
     "ed_hash_base": (_U64, [_P]),
     "ed_frontiers_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _P, _P]),
     "ed_edit_script_dev": (_I, [_P, _P, _S, _P, _S, _I64, _P, _S, _P, _P, _P]),
+    "ed_trace_script": (_I, [_P, _I64, _S, _S, _U64, _P, _S, _P]),
     "ed_prefix_hash_noalloc": (_I, [_P, _S, _U64, _P, _P]),
 }
 
@@ -348,6 +349,17 @@ def ed_edit_script_dev(ctx, A, B, t_max: int, stream=None):
     _check(ctx, load().ed_edit_script_dev(ctx, pa, n, pb, m, t_max, ops.ctypes.data, t_max, ctypes.byref(nops),
                                           ctypes.byref(k), _stream_ptr(stream)), "ed_edit_script_dev")
     return int(k.value), ops[: int(nops.value)].copy()
+
+
+def ed_trace_script(F, t_max: int, n: int, m: int, k: int):
+    """ops (k, 3) int64 traced back from host frontiers F[t, d + t_max] = L_t[d]."""
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    assert F.shape[1] == 2 * t_max + 1 and F.shape[0] >= k + 1
+    ops = np.zeros((max(k, 1), 3), dtype=np.int64)
+    nops = ctypes.c_size_t()
+    _check(None, load().ed_trace_script(F.ctypes.data, t_max, n, m, k, ops.ctypes.data, k, ctypes.byref(nops)),
+           "ed_trace_script")
+    return ops[: int(nops.value)].copy()
 
 
 class Context:

@@ -794,6 +794,8 @@ static bool trace_script(const int32_t *F, int64_t T, int64_t n, int64_t m, int6
         return v < 0 ? NONE : (int64_t)v;
     };
     int64_t x = n, y = m, t = k;
+    if (L(k, m - n) != n) // (n, m) is not reached in round k
+        return false;
     while (x > 0 || y > 0) {
         const int64_t d = y - x;
         if (t == 0) // the slide of round 0 from (0, 0)
@@ -856,14 +858,24 @@ int ed_edit_script_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B
         return ED_ELIMIT;
     if (cap < kk)
         return ED_EINVAL;
+    // frontiers that contradict themselves would be a device fault
+    return ed_trace_script(F.data(), t_max, n, m, kk, ops, cap, nops) == ED_OK ? ED_OK : ED_ECUDA;
+}
+
+int ed_trace_script(const int32_t *F, int64_t t_max, size_t n, size_t m, uint64_t k, int64_t *ops, size_t cap,
+                    size_t *nops)
+{
+    if (!F || !nops || (cap && !ops) || t_max < 0 || k > (uint64_t)t_max || cap < k || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    *nops = 0;
     std::vector<int64_t> back;
-    back.reserve(3 * (size_t)kk);
-    if (!trace_script(F.data(), t_max, (int64_t)n, (int64_t)m, (int64_t)kk, back) || back.size() != 3 * kk)
-        return ED_ECUDA; // frontiers that contradict themselves: a device fault
-    for (size_t i = 0; i < kk; i++)
+    back.reserve(3 * (size_t)k);
+    if (!trace_script(F, t_max, (int64_t)n, (int64_t)m, (int64_t)k, back) || back.size() != 3 * k)
+        return ED_EINVAL;
+    for (size_t i = 0; i < k; i++)
         for (int j = 0; j < 3; j++)
-            ops[3 * i + j] = back[3 * (kk - 1 - i) + j];
-    *nops = (size_t)kk;
+            ops[3 * i + j] = back[3 * (k - 1 - i) + j];
+    *nops = (size_t)k;
     return ED_OK;
 }
 
