@@ -226,8 +226,9 @@ int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n,
                      const uint8_t *B, size_t m, int64_t t_max, int32_t *out,
                      uint64_t *k, void *stream);
 
-/* Edit operations of ed_edit_script_dev. */
+/* Edit operations of ed_edit_script_dev, and its bound on t_max. */
 enum { ED_OP_SUB = 0, ED_OP_DEL = 1, ED_OP_INS = 2 };
+#define ED_SCRIPT_MAX_ROUNDS 16384
 
 /* An optimal edit script of A into B (DEVICE strings), traced back from
  * the frontiers of rounds 0..k of Algorithm 1 (Sec. 3.1): a cell on
@@ -238,9 +239,10 @@ enum { ED_OP_SUB = 0, ED_OP_DEL = 1, ED_OP_INS = 2 };
  * order they apply from the start of the strings: ED_OP_SUB puts B[y] in
  * place of A[x], ED_OP_DEL deletes A[x], ED_OP_INS inserts B[y] before A[x];
  * the characters between two operations match.  *nops = *k operations.
- * Needs k <= t_max <= 4096 (the frontiers take (t_max+1)(2 t_max+1) int32
- * of device memory, kept in the context): ED_ELIMIT with *k = UINT64_MAX
- * when k > t_max.  ops has room for cap operations (3 int64 each); cap <
+ * Needs k <= t_max <= ED_SCRIPT_MAX_ROUNDS.  The frontiers take (t_max+1)
+ * (2 t_max+1) int32 of device memory, kept in the context, and as much host
+ * memory during the call (2.1 GB each at the bound; ED_ENOMEM when either
+ * cannot be had).  ED_ELIMIT with *k = UINT64_MAX when k > t_max.  ops has room for cap operations (3 int64 each); cap <
  * k returns ED_EINVAL with *k set.  Any script it returns is one of the
  * optimal ones (several may exist).  Synchronous on `stream`. */
 int ed_edit_script_dev(ed_ctx *ctx, const uint8_t *A, size_t n,

@@ -15,6 +15,7 @@
 #include <deque>
 #include <map>
 #include <memory>
+#include <new>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -750,10 +751,12 @@ int ed_distance(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_
                     ctx->stream, nullptr, 0, k);
 }
 
-int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
-                     int32_t *out, uint64_t *k, void *stream)
+// The frontiers of rounds 0..t_max into the host array out (ed_frontiers_dev
+// up to t_max_limit rounds).
+static int frontiers_to_host(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
+                             int32_t *out, uint64_t *k, void *stream, int64_t t_max_limit)
 {
-    if (!ctx || !k || !out || t_max < 0 || t_max > 4096 || (n && !A) || (m && !B) || bad_len(n) ||
+    if (!ctx || !k || !out || t_max < 0 || t_max > t_max_limit || (n && !A) || (m && !B) || bad_len(n) ||
         bad_len(m))
         return ED_EINVAL;
     std::lock_guard<std::mutex> g(ctx->api_mu);
@@ -777,6 +780,12 @@ int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, 
             out[t * (2 * t_max + 1) + i] = (int32_t)0xC0C0C0C0;
     *k = kk <= (uint64_t)t_max ? kk : UINT64_MAX;
     return ED_OK;
+}
+
+int ed_frontiers_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
+                     int32_t *out, uint64_t *k, void *stream)
+{
+    return frontiers_to_host(ctx, A, n, B, m, t_max, out, k, stream, 4096);
 }
 
 // The walk back of ed_edit_script_dev over the frontiers F (rows 0..k of
@@ -844,12 +853,17 @@ static bool trace_script(const int32_t *F, int64_t T, int64_t n, int64_t m, int6
 int ed_edit_script_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, int64_t t_max,
                        int64_t *ops, size_t cap, size_t *nops, uint64_t *k, void *stream)
 {
-    if (!ctx || !k || !nops || (cap && !ops) || t_max < 0 || t_max > 4096 || (n && !A) || (m && !B) ||
-        bad_len(n) || bad_len(m))
+    if (!ctx || !k || !nops || (cap && !ops) || t_max < 0 || t_max > ED_SCRIPT_MAX_ROUNDS || (n && !A) ||
+        (m && !B) || bad_len(n) || bad_len(m))
         return ED_EINVAL;
-    std::vector<int32_t> F((size_t)(t_max + 1) * (size_t)(2 * t_max + 1));
+    std::vector<int32_t> F;
+    try {
+        F.resize((size_t)(t_max + 1) * (size_t)(2 * t_max + 1));
+    } catch (const std::bad_alloc &) {
+        return ED_ENOMEM;
+    }
     uint64_t kk = 0;
-    int r = ed_frontiers_dev(ctx, A, n, B, m, t_max, F.data(), &kk, stream);
+    int r = frontiers_to_host(ctx, A, n, B, m, t_max, F.data(), &kk, stream, ED_SCRIPT_MAX_ROUNDS);
     if (r != ED_OK)
         return r;
     *k = kk;

@@ -64,6 +64,12 @@ def test_long_pair_near_the_bound(ctxs, orc):
     _check(ctxs["default"], orc, p.A, p.B, slack=1)
 
 
+def test_distance_past_the_frontier_dump_bound(ctxs, orc):
+    # k ~ 6000: past the 4096 rounds of ed_frontiers_dev, within the script's bound
+    p = W.make_pair(34, 2_000_000, 6000, sigma=4)
+    _check(ctxs["default"], orc, p.A, p.B, slack=1)
+
+
 def test_distance_past_the_bound_is_reported(ctxs, orc):
     from paper_2306_17461_gb300 import binding as ed
 
