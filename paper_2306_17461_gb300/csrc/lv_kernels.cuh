@@ -15,19 +15,18 @@ constexpr uint32_t ST_SUSPENDED = 9; // per pair: budget spent, frontier saved t
 constexpr int CTA_THREADS = 256;   // threads of a tile CTA (up to 255 registers each)
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
 constexpr int HMAX = 16;           // rounds per temporal block, at most
-constexpr int CHUNK_UNROLL = 8;
 constexpr int CHUNK_BYTES = 64 * 1024; // bytes of one job-slot claim
 constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
-constexpr uint32_t CLAIM_CLOSED = 0xffffffffu;
 constexpr int MAX_CLS = 12;        // group-size classes of one tile launch
 // done_k of a pair that ended without a distance (status in its R_STATUS)
 constexpr unsigned long long DONE_STOPPED = ~0ull - 1;
 
 // A long slide open for help.  Each CTA owns one slot.  `claim` packs the
-// job id (high 32 bits) and the next unclaimed 64 KiB chunk (low 32 bits,
-// CLAIM_CLOSED once the owner closed it); chunks are claimed by CAS in
-// increasing order; `result` (first mismatch offset, starts at lim) falls
-// by atomicMin; `done` counts finished claims.
+// job id (high 32 bits) and the count of claims made (low 32 bits): every
+// atomicAdd of 1 claims the next 64 KiB chunk, and the owner closes the job
+// by adding a high bit to the count (the protocol is in lv_tiles.cu);
+// `result` (first mismatch offset, starts at lim) falls by atomicMin;
+// `done` counts answered claims.
 struct __align__(128) JobSlot {
     unsigned long long claim;
     unsigned long long result;

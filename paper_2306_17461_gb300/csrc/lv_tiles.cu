@@ -21,13 +21,16 @@
 //    its two neighbours through global memory and a per-CTA release flag.
 //    There is no grid-wide barrier per round, only neighbour waits every h
 //    rounds.
+//  * Pipelined rounds: within a block, six warps compute round t while two
+//    slider warps finish the open slides of round t - 1 and then the
+//    diagonals beside them; two CTA barriers a round (run_block).
 //  * Slides: one thread compares the two aligned 4-byte words at each start
 //    row (at least five bytes; several diagonals' loads in flight
 //    together); slides that match all of them go to one warp each (ballot /
 //    first set bit over 2 KiB steps, prefetching the next 4 KiB into L2 when
 //    done, where the next round starts), then, if still open after t2_cap
 //    bytes, to the whole CTA, which scans 64 KiB per step with every load in
-//    flight.  A slide still open
+//    flight (after one bulk L2 prefetch of what it scans).  A slide still open
 //    after LOCAL_STEPS such steps becomes a job in the CTA's job slot: its
 //    64 KiB chunks are claimed by atomicAdd by the owner and by every CTA
 //    that is waiting on a neighbour or has no tile; the first mismatch is the
