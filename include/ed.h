@@ -66,7 +66,8 @@ typedef struct {
     uint64_t spin_limit_ns;   /* bound of every device-side wait; 0 = 2e9 */
     int grid_ctas;            /* CTAs of the tile kernel; 0 = one per SM */
     int tile_width;           /* diagonals per CTA in the first epoch (the
-                                 tiles double with the band); 0 = 64 */
+                                 tiles grow with the band, by an eighth at
+                                 a time); 0 = 64 */
     int block_rounds;         /* rounds between neighbour exchanges (1..16);
                                  0 = 16 */
     int64_t max_rounds;       /* frontier capacity in rounds; 0 = the larger
