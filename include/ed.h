@@ -156,6 +156,18 @@ int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
               size_t m, uint64_t *ticket);
 int ed_poll(ed_ctx *ctx, uint64_t ticket, uint64_t *k);
 
+/* ed_submit for DEVICE strings A, B (memory of the context's device, any
+ * alignment) produced on `stream` (a cudaStream_t; NULL = legacy default):
+ * the pair is admitted like ed_submit's (a serving slot and its resident
+ * frontier in the arena; ED_EBUSY when either is missing) but its strings
+ * are not copied: the engine reads the caller's buffers, after the work
+ * queued on `stream` before this call (an event recorded on it), so the
+ * caller may submit strings that a kernel of its own is still writing.  A
+ * and B must stay alive and unchanged until ed_poll returns ED_OK (or an
+ * error) for the ticket.  Returns at once; results through ed_poll. */
+int ed_submit_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
+                  size_t m, uint64_t *ticket, void *stream);
+
 /* Serving counters: admitted, completed, in flight, engine steps, and
  * slices (times a pair on the tile kernel was left at a sync point with its
  * band frontier saved, to be resumed at the next step).  Null pointers are
@@ -180,7 +192,9 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
 
 /* The prefix table of Sec. 3.2: T[i] = sum_{j<i} (X[j]+1) * p^(i-1-j)
  * mod 2^61-1 for i = 0..len, p = ed_hash_base(ctx).  X and T are device
- * pointers; T has len + 1 uint64 entries.  One single-pass scan launch. */
+ * pointers; T has len + 1 uint64 entries.  One single-pass scan launch;
+ * synchronous on `stream`.  ED_ETIMEOUT when a bounded wait of the scan
+ * gave up (the table is then not valid). */
 int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T,
                        void *stream);
 
@@ -188,7 +202,7 @@ int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T,
  * j = 0..len/b, the entries of ed_prefix_hash_dev's table at multiples of
  * b (1 <= b <= 2^20).  X and T are device pointers; T has len/b + 1 uint64
  * entries.  One scan launch that writes only the block prefixes.
- * Synchronous on `stream`. */
+ * Synchronous on `stream`; ED_ETIMEOUT as for ed_prefix_hash_dev. */
 int ed_prefix_hash_blocked_dev(ed_ctx *ctx, const uint8_t *X, size_t len, size_t b, uint64_t *T,
                                void *stream);
 
@@ -209,13 +223,17 @@ uint64_t ed_hash_base(ed_ctx *ctx);
  * fixed 1 MiB array compiled into the library, which every GPU that loads
  * the library keeps until the process exits.  The paper has no counterpart;
  * the table computed is the same as ed_prefix_hash_dev's with the given
- * base.  X and T are device pointers (T: len + 1 uint64 entries); base must
- * lie in [2, 2^61-2].  len above ED_NOALLOC_MAX_LEN returns ED_EINVAL.  The
+ * base.  X and T are device pointers (T: len + 1 uint64 entries) of the
+ * CURRENT device, and `stream` belongs to it; the call must run in that
+ * device's primary context (the CUDA runtime's own; the array's address is
+ * looked up once per device ordinal in it).  base must lie in
+ * [2, 2^61-2].  len above ED_NOALLOC_MAX_LEN returns ED_EINVAL.  The
  * first call on a device looks up the array's device address (make that
  * call before any stream capture).  Every call shares the array and clears
  * it on `stream` before use: calls whose work overlaps on the GPU (two
  * streams, or two threads) race and must be serialised by the caller.
- * Synchronous on `stream` (NULL = legacy default). */
+ * Synchronous on `stream` (NULL = legacy default).  ED_ETIMEOUT when a
+ * bounded wait of the scan gave up (the table is then not valid). */
 int ed_prefix_hash_noalloc(const uint8_t *X, size_t len, uint64_t base, uint64_t *T,
                            void *stream);
 

@@ -80,6 +80,7 @@ _SIGS = {
     "ed_distance_batch_dev": (_I, [_P, _S, _P, _P, _P, _P, _P, _P]),
     "ed_distance_batch": (_I, [_P, _S, _P, _P, _P, _P, _P]),
     "ed_submit": (_I, [_P, _P, _S, _P, _S, _P]),
+    "ed_submit_dev": (_I, [_P, _P, _S, _P, _S, _P, _P]),
     "ed_poll": (_I, [_P, _U64, _P]),
     "ed_serve_counters": (_I, [_P, _P, _P, _P, _P, _P]),
     "ed_lcp_dev": (_I, [_P, _P, _S, _P, _S, _P, _P, _S, _I, _P, _P, _P, _P]),
@@ -255,6 +256,16 @@ def ed_submit(ctx, A, B) -> int:
     return int(t.value)
 
 
+def ed_submit_dev(ctx, A, B, stream=None) -> int:
+    """Submits device strings (CUDA uint8 tensors) written on `stream`;
+    they must stay alive until the ticket is polled done."""
+    pa, n = _dev_buf(A)
+    pb, m = _dev_buf(B)
+    t = ctypes.c_uint64()
+    _check(ctx, load().ed_submit_dev(ctx, pa, n, pb, m, ctypes.byref(t), _stream_ptr(stream)), "ed_submit_dev")
+    return int(t.value)
+
+
 def ed_poll(ctx, ticket: int):
     """(status, k): status ED_OK with k, or ED_EAGAIN; errors raise."""
     k = ctypes.c_uint64()
@@ -315,12 +326,25 @@ ED_NOALLOC_MAX_LEN = 89468928
 
 def ed_prefix_hash_noalloc(X, base: int, T, stream=None) -> None:
     """The prefix table of X into the caller's CUDA tensor T (int64, len+1
-    entries) without any allocation by the library (include/ed.h)."""
+    entries) without any allocation by the library (include/ed.h).  X, T
+    and the stream must be on one device; the call runs with that device
+    current."""
+    import torch
+
     px, n = _dev_buf(X)
-    if T.numel() != n + 1 or not T.is_cuda or T.element_size() != 8:
+    if not isinstance(T, torch.Tensor) or not T.is_cuda or T.element_size() != 8 or T.numel() != n + 1:
         raise ValueError("T must be a CUDA tensor of len(X) + 1 8-byte entries")
-    _check(None, load().ed_prefix_hash_noalloc(px, n, base, T.data_ptr(), _stream_ptr(stream)),
-           "ed_prefix_hash_noalloc")
+    if not T.is_contiguous():
+        raise ValueError("T must be contiguous")
+    if T.device != X.device:
+        raise ValueError("X and T must be on the same device")
+    with torch.cuda.device(X.device):
+        if stream is None:
+            stream = torch.cuda.current_stream(X.device)
+        elif stream.device != X.device:
+            raise ValueError("the stream must belong to the device of X and T")
+        _check(None, load().ed_prefix_hash_noalloc(px, n, base, T.data_ptr(), _stream_ptr(stream)),
+               "ed_prefix_hash_noalloc")
 
 
 def ed_frontiers_dev(ctx, A, B, t_max: int, stream=None):

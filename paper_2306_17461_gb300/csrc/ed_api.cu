@@ -110,6 +110,10 @@ struct Request {
     uint64_t ticket = 0;
     char *dA = nullptr, *dB = nullptr, *front = nullptr;
     size_t bytesA = 0, bytesB = 0, bytesF = 0;
+    // ed_submit_dev: the strings are the caller's (not in the arena), ready
+    // once `ready` (recorded on the caller's stream) has completed
+    bool caller_strings = false;
+    cudaEvent_t ready = nullptr;
     int64_t n = 0, m = 0;
     int32_t t = -1;
     // on the tile kernel (band wider than one batch CTA): its group size,
@@ -273,6 +277,22 @@ int64_t hash_stride(const ed_ctx *ctx)
     return ctx->cfg.lcp_mode == ED_LCP_BHASH ? (int64_t)ctx->cfg.hash_block : 1;
 }
 
+// Waits for the prefix-hash scan last launched on s with the context's scan
+// state and maps its status word: a look-back wait that gave up leaves a
+// wrong table, reported as ED_ETIMEOUT.
+int scan_result(ed_ctx *ctx, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    const uint32_t st = prefix_hash_status(ctx->scan.p, s, &e);
+    if (e != cudaSuccess)
+        return cuda_fail(ctx, e, "prefix hash scan");
+    if (st != 0) {
+        ctx->last_err = "prefix hash scan: a look-back wait gave up";
+        return status_from_kernel(st);
+    }
+    return ED_OK;
+}
+
 int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB, int64_t m,
                     cudaStream_t s)
 {
@@ -287,8 +307,12 @@ int run_hash_tables(ed_ctx *ctx, const uint8_t *dA, int64_t n, const uint8_t *dB
         return r;
     CK(launch_prefix_hash(dA, n, ctx->hash_base, (uint64_t *)ctx->hashA.p, b, ctx->scan.p,
                           prefix_hash_state_bytes(n), s));
+    if ((r = scan_result(ctx, s)) != ED_OK)
+        return r;
     CK(launch_prefix_hash(dB, m, ctx->hash_base, (uint64_t *)ctx->hashB.p, b, ctx->scan.p,
                           prefix_hash_state_bytes(m), s));
+    if ((r = scan_result(ctx, s)) != ED_OK)
+        return r;
     ctx->last.kernel_launches += 2;
     return ED_OK;
 }
@@ -453,6 +477,8 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.idle_ns = ctx->cfg.spin_limit_ns * 60;
     P.budget_ns = budget_ns;
     P.sync_rounds = 16 * h;
+    P.help_div = 8;
+    P.local_chunks = 1;
     CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->ctl.p, 0, sizeof(LaunchCtl), s));
     CK(cudaMemsetAsync(ctx->gctl.p, 0, sizeof(GroupCtl) * ngroups, s));
@@ -905,8 +931,7 @@ int ed_prefix_hash_dev(ed_ctx *ctx, const uint8_t *X, size_t len, uint64_t *T, v
         return r;
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, 1, ctx->scan.p, sb, s));
-    CK(cudaStreamSynchronize(s));
-    return ED_OK;
+    return scan_result(ctx, s);
 }
 
 int ed_prefix_hash_blocked_dev(ed_ctx *ctx, const uint8_t *X, size_t len, size_t b, uint64_t *T, void *stream)
@@ -921,8 +946,7 @@ int ed_prefix_hash_blocked_dev(ed_ctx *ctx, const uint8_t *X, size_t len, size_t
         return r;
     cudaStream_t s = (cudaStream_t)stream;
     CK(launch_prefix_hash(X, (int64_t)len, ctx->hash_base, T, (int64_t)b, ctx->scan.p, sb, s));
-    CK(cudaStreamSynchronize(s));
-    return ED_OK;
+    return scan_result(ctx, s);
 }
 
 int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, const int64_t *x,
@@ -1207,10 +1231,15 @@ constexpr uint64_t SERVE_TILE_NS = 4000000;
 
 static void release_request(ed_ctx *ctx, Request *q)
 {
-    ctx->arena.release(q->dA, q->bytesA);
-    ctx->arena.release(q->dB, q->bytesB);
+    if (!q->caller_strings) {
+        ctx->arena.release(q->dA, q->bytesA);
+        ctx->arena.release(q->dB, q->bytesB);
+    }
     ctx->arena.release(q->front, q->bytesF);
     ctx->arena.release(q->keep, q->bytesK);
+    if (q->ready)
+        cudaEventDestroy(q->ready);
+    q->ready = nullptr;
 }
 
 // Moves a request to the tile kernel on a group of G CTAs, with a resident
@@ -1246,7 +1275,12 @@ static void engine_loop(ed_ctx *ctx)
             if (ctx->stop)
                 break;
             while (!ctx->pending.empty()) {
-                ctx->live.push_back(ctx->pending.front());
+                Request *q = ctx->pending.front();
+                // device strings of the caller: the engine's stream waits for
+                // the work the caller queued before submitting them
+                if (q->ready)
+                    cudaStreamWaitEvent(ctx->sstream, q->ready, 0);
+                ctx->live.push_back(q);
                 ctx->pending.pop_front();
             }
         }
@@ -1407,10 +1441,16 @@ static void engine_stop(ed_ctx *ctx)
     ctx->scv.notify_all();
     ctx->engine.join();
     ctx->engine_on = false;
-    for (Request *q : ctx->live)
+    for (Request *q : ctx->live) {
+        if (q->ready)
+            cudaEventDestroy(q->ready);
         delete q;
-    for (Request *q : ctx->pending)
+    }
+    for (Request *q : ctx->pending) {
+        if (q->ready)
+            cudaEventDestroy(q->ready);
         delete q;
+    }
     ctx->live.clear();
     ctx->pending.clear();
     if (ctx->sstream)
@@ -1461,6 +1501,52 @@ int ed_submit(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t 
         ctx->arena.release(q->front, q->bytesF);
         delete q;
         return cuda_fail(ctx, e, "ed_submit copy");
+    }
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        q->ticket = ctx->next_ticket++;
+        ctx->known[q->ticket] = true;
+        ctx->pending.push_back(q);
+        ctx->n_admitted++;
+        *ticket = q->ticket;
+    }
+    ctx->scv.notify_all();
+    return ED_OK;
+}
+
+int ed_submit_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t m, uint64_t *ticket,
+                  void *stream)
+{
+    if (!ctx || !ticket || (n && !A) || (m && !B) || bad_len(n) || bad_len(m))
+        return ED_EINVAL;
+    int r = engine_start(ctx);
+    if (r != ED_OK)
+        return r;
+    {
+        std::lock_guard<std::mutex> lk(ctx->smu);
+        if (ctx->live.size() + ctx->pending.size() >= (size_t)ctx->cfg.max_inflight)
+            return ED_EBUSY;
+    }
+    Request *q = new Request();
+    q->n = (int64_t)n;
+    q->m = (int64_t)m;
+    q->caller_strings = true;
+    q->dA = (char *)A;
+    q->dB = (char *)B;
+    q->bytesF = sizeof(int32_t) * (BATCH_W + 3);
+    q->front = ctx->arena.alloc(q->bytesF);
+    if (!q->front) {
+        delete q;
+        return ED_EBUSY;
+    }
+    cudaSetDevice(ctx->device);
+    cudaError_t e = cudaEventCreateWithFlags(&q->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(q->ready, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        release_request(ctx, q);
+        delete q;
+        return cuda_fail(ctx, e, "ed_submit_dev event");
     }
     {
         std::lock_guard<std::mutex> lk(ctx->smu);

@@ -409,6 +409,114 @@ __device__ __forceinline__ int64_t cta_scan(const uint8_t *A, int64_t n, const u
     return r == ~0ull ? -1 : (int64_t)r;
 }
 
+// ------------------------------------------------------- CTA sweep
+// An aligned 16-byte block loaded past the L1 (the bytes of a long slide are
+// read once; the L1 keeps the lines the rounds' start rows reuse).
+__device__ __forceinline__ uint4 ld_stream16(uintptr_t p)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
+    return v;
+}
+
+// The aligned block at blk if it overlaps [base, base + len) (len > 0),
+// else the block holding the string's first or last byte: a block that
+// overlaps the string lies in the same page as a valid byte and cannot
+// fault.  Bytes outside the window a caller asked for are masked by it.
+__device__ __forceinline__ uintptr_t safe_blk(uintptr_t base, int64_t len, uintptr_t blk)
+{
+    const uintptr_t first = base & ~(uintptr_t)15, last = (base + (uintptr_t)len - 1) & ~(uintptr_t)15;
+    return blk < first ? first : (blk > last ? last : blk);
+}
+
+// The calling CTA compares A[x0 .. x0+len) with B[y0 .. y0+len) for
+// len <= blockDim.x * 16 * U (32 KiB per string at 256 threads, U = 8) and
+// returns the first mismatching offset, or -1 if all are equal.  Needs
+// x0 + len <= n and y0 + len <= m.  Every load is issued before the first
+// compare: one memory round trip per call.
+//
+// The A side is read in aligned 16-byte blocks: block j starts sa bytes
+// before A[x0] (sa = the misalignment of A + x0) and holds offsets
+// 16j - sa .. 16j - sa + 15.  The B bytes paired with them are bytes
+// qb .. qb + 15 of the 32-byte run made of B's aligned blocks j and j + 1
+// (counted from the block holding B[y0 - sa]); block j + 1 belongs to the
+// next lane, so it comes by shuffle (lane 31 takes the next row of blocks,
+// or one extra load after the last).  Warp w reads 32 * U consecutive
+// blocks.  Every thread must call it; s_min is a shared 64-bit scratch word.
+template <int U>
+__device__ __forceinline__ int64_t sweep_scan(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m, int64_t x0,
+                                              int64_t y0, int64_t len, unsigned long long *s_min)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0)
+        *s_min = ~0ull;
+    const uintptr_t pa = (uintptr_t)(A + x0);
+    const uint32_t sa = (uint32_t)(pa & 15);
+    const uintptr_t a0 = pa - sa;
+    const uintptr_t pbs = (uintptr_t)(B + y0) - sa; // B address paired with a0
+    const uint32_t qb = (uint32_t)(pbs & 15);
+    const uintptr_t b0 = pbs - qb;
+    const uintptr_t Ab = (uintptr_t)A, Bb = (uintptr_t)B;
+    const int64_t jw = (int64_t)warp * 32 * U; // this warp's first block
+    uint4 va[U], vb[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        const int64_t j = jw + u * 32 + lane;
+        va[u] = ld_stream16(safe_blk(Ab, n, a0 + 16 * j));
+        vb[u] = ld_stream16(safe_blk(Bb, m, b0 + 16 * j));
+    }
+    const uint4 vx = ld_stream16(safe_blk(Bb, m, b0 + 16 * (jw + 32 * U)));
+    int64_t best = -1;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        // the B block after this lane's: the next lane's, or for lane 31 the
+        // first of the next row (the extra block after the last row)
+        const uint4 nb = u + 1 < U ? vb[u + 1] : vx;
+        uint4 nx;
+        nx.x = __shfl_down_sync(0xffffffffu, vb[u].x, 1);
+        nx.y = __shfl_down_sync(0xffffffffu, vb[u].y, 1);
+        nx.z = __shfl_down_sync(0xffffffffu, vb[u].z, 1);
+        nx.w = __shfl_down_sync(0xffffffffu, vb[u].w, 1);
+        const uint4 f0 = make_uint4(__shfl_sync(0xffffffffu, nb.x, 0), __shfl_sync(0xffffffffu, nb.y, 0),
+                                    __shfl_sync(0xffffffffu, nb.z, 0), __shfl_sync(0xffffffffu, nb.w, 0));
+        if (lane == 31)
+            nx = f0;
+        const uint4 bs = shift_bytes(vb[u], nx, qb);
+        const int64_t j = jw + u * 32 + lane;
+        // valid bytes of this block: offsets 16j - sa + i in [0, len)
+        const int64_t o0 = 16 * j - (int64_t)sa;
+        const int lo = o0 < 0 ? (int)-o0 : 0;
+        const int64_t hi64 = len - o0;
+        const int hi = hi64 >= 16 ? 16 : (hi64 <= 0 ? 0 : (int)hi64);
+        if (best < 0 && lo < hi) {
+            uint64_t d0 = ((uint64_t)(va[u].y ^ bs.y) << 32) | (uint64_t)(va[u].x ^ bs.x);
+            uint64_t d1 = ((uint64_t)(va[u].w ^ bs.w) << 32) | (uint64_t)(va[u].z ^ bs.z);
+            // keep bytes lo .. hi-1
+            const uint64_t k0lo = lo >= 8 ? 0ull : (~0ull << (8 * lo));
+            const uint64_t k1lo = lo <= 8 ? ~0ull : (~0ull << (8 * (lo - 8)));
+            const uint64_t k0hi = hi >= 8 ? ~0ull : ((1ull << (8 * hi)) - 1ull);
+            const uint64_t k1hi = hi <= 8 ? 0ull : (hi >= 16 ? ~0ull : ((1ull << (8 * (hi - 8))) - 1ull));
+            d0 &= k0lo & k0hi;
+            d1 &= k1lo & k1hi;
+            if (d0)
+                best = o0 + ((__ffsll((long long)d0) - 1) >> 3);
+            else if (d1)
+                best = o0 + 8 + ((__ffsll((long long)d1) - 1) >> 3);
+        }
+    }
+    if (__syncthreads_or(best >= 0)) {
+        if (best >= 0)
+            atomicMin(s_min, (unsigned long long)best);
+        __syncthreads();
+        const int64_t r = (int64_t)*s_min;
+        __syncthreads(); // read by all before the next call resets it
+        return r;
+    }
+    return -1;
+}
+
 // ------------------------------------------------------- mod 2^61 - 1
 // a * b mod q for a, b < q: the 122-bit product hi:lo splits as
 // (hi << 3 | lo >> 61) * 2^61 + (lo & q), and 2^61 = 1 (mod q).

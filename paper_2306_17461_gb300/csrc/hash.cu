@@ -14,6 +14,8 @@
 // 8 bytes per character; with an output stride b > 1 it writes only the
 // prefixes of whole blocks, T[j] = h(X[0..jb)), the blocked table of
 // Sec. 3.3 (Alg. 2), 8/b bytes per character.
+#include <cstddef>
+
 #include "ed_device.cuh"
 #include "lv_kernels.cuh"
 
@@ -176,6 +178,18 @@ __global__ void __launch_bounds__(HT) prefix_hash_kernel(const uint8_t *X, int64
 
 }
 
+uint32_t prefix_hash_status(const void *scan_state, cudaStream_t s, cudaError_t *e)
+{
+    // the scan's status word (ST_TIMEOUT when a look-back wait gave up and
+    // the table after that tile is wrong), copied to the host stack
+    uint32_t st = 0;
+    *e = cudaMemcpyAsync(&st, static_cast<const unsigned char *>(scan_state) + offsetof(ScanState, error),
+                         sizeof(st), cudaMemcpyDeviceToHost, s);
+    if (*e == cudaSuccess)
+        *e = cudaStreamSynchronize(s);
+    return st;
+}
+
 cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T, int64_t stride,
                                void *scan_state, size_t scan_state_bytes, cudaStream_t s)
 {
@@ -244,7 +258,9 @@ extern "C" int ed_prefix_hash_noalloc(const uint8_t *X, size_t len, uint64_t bas
     // the look-back descriptors must start at zero: cleared on every call
     if (edg::launch_prefix_hash(X, (int64_t)len, base, T, 1, scratch, need, s) != cudaSuccess)
         return ED_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess)
+    cudaError_t e = cudaSuccess;
+    const uint32_t st = edg::prefix_hash_status(scratch, s, &e);
+    if (e != cudaSuccess)
         return ED_ECUDA;
-    return ED_OK;
+    return st == 0 ? ED_OK : (st == edg::ST_TIMEOUT ? ED_ETIMEOUT : ED_ECUDA);
 }

@@ -15,7 +15,7 @@ constexpr uint32_t ST_SUSPENDED = 9; // per pair: budget spent, frontier saved t
 constexpr int CTA_THREADS = 256;   // threads of a tile CTA (up to 255 registers each)
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
 constexpr int HMAX = 16;           // rounds per temporal block, at most
-constexpr int CHUNK_BYTES = 64 * 1024; // bytes of one job-slot claim
+constexpr int CHUNK_BYTES = 32 * 1024; // bytes of one job-slot claim (per string)
 constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
 constexpr int MAX_CLS = 12;        // group-size classes of one tile launch
 // done_k of a pair that ended without a distance (status in its R_STATUS)
@@ -23,7 +23,7 @@ constexpr unsigned long long DONE_STOPPED = ~0ull - 1;
 
 // A long slide open for help.  Each CTA owns one slot.  `claim` packs the
 // job id (high 32 bits) and the count of claims made (low 32 bits): every
-// atomicAdd of 1 claims the next 64 KiB chunk, and the owner closes the job
+// atomicAdd of 1 claims the next chunk (CHUNK_BYTES of each string), and the owner closes the job
 // by adding a high bit to the count (the protocol is in lv_tiles.cu);
 // `result` (first mismatch offset, starts at lim) falls by atomicMin;
 // `done` counts answered claims.
@@ -130,6 +130,11 @@ struct LvArgs {
     // once budget_ns have passed since the launch started
     uint64_t budget_ns;
     int32_t sync_rounds;
+    // while a group's band is narrow, G / help_div of its CTAs (groups of at
+    // least 2 * help_div CTAs) hold no tile and serve long slides (0: none)
+    int32_t help_div;
+    // chunks of a long slide its CTA scans alone before publishing the rest
+    int32_t local_chunks;
 };
 
 size_t lv_tiles_smem_bytes(int smax, int h);
@@ -190,5 +195,9 @@ cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, in
 cudaError_t launch_prefix_hash(const uint8_t *X, int64_t len, uint64_t base, uint64_t *T, int64_t stride,
                                void *scan_state, size_t scan_state_bytes, cudaStream_t s);
 size_t prefix_hash_state_bytes(int64_t len);
+// After a launch_prefix_hash on s: waits for s and returns the scan's status
+// word (0, or ST_TIMEOUT when a bounded look-back wait gave up); *e gets the
+// CUDA error of the copy or the wait.
+uint32_t prefix_hash_status(const void *scan_state, cudaStream_t s, cudaError_t *e);
 
 } // namespace edg

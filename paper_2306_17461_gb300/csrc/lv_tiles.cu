@@ -43,7 +43,6 @@
 
 namespace edg {
 
-constexpr int LOCAL_STEPS = 2;            // 64 KiB steps the owner takes alone
 constexpr int64_t GROW_NUM = 9, GROW_DEN = 8; // epoch radius growth factor
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 
@@ -180,6 +179,9 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
+// Orders the relaxed loads before it ahead of every access after it (the
+// acquire half of a flag handshake whose writer used a release).
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 __device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v)
 {
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -207,6 +209,15 @@ __device__ __noinline__ void wait_failed(const LvArgs &P, unsigned long long sit
     }
 }
 
+// A helper CTA's copy of the job it claims from (read once per job).
+struct JobDesc {
+    const uint8_t *A, *B;
+    long long n, m, x, y, lim;
+    uint32_t jid;
+    int32_t slot;
+};
+static_assert(sizeof(JobDesc) <= 64, "the job cache fills bytes 192..255 of the smem header");
+
 // Kept in registers: every function takes it by value (no address taken,
 // no array member indexed at run time).
 struct Smem {
@@ -223,152 +234,196 @@ struct Smem {
     int *bc;            // 8 broadcast words
     long long *bcl;     // 4 broadcast 64-bit words
     unsigned long long *smin;
+    JobDesc *jd;        // the job last claimed from
     int lcap;
     uint32_t *err;             // launch status word (self-check records)
     unsigned long long *diag;
 };
 
 // Job slot protocol.  claim = (job id << 32) | count.  Every atomicAdd of 1
-// is one claim of chunk `count`; a claim whose count has CLAIM_CLOSE set
-// arrived after the owner closed the job and is void.  Each valid claim is
-// answered by exactly one increment of `done` (after scanning the chunk, or
-// at once when the chunk lies past the end or past the best mismatch).  A
-// claim that lands on a job published after the claimer looked is still a
-// valid claim of that job: the descriptor read after the atomic is that
-// job's, because the slot cannot be republished before `done` covers it.
-// Returns the chunk index (>= 0) with the job's descriptor in the slot, or
-// -1 when the claim is void.
-__device__ __forceinline__ int64_t claim_chunk(JobSlot *sl)
+// is one claim of chunk `count` (CHUNK_BYTES of each string); a claim whose
+// count has CLAIM_CLOSE set arrived after the owner closed the job and is
+// void.  Each valid claim is answered by exactly one increment of `done`
+// (after scanning the chunk, or at once when the chunk lies past the end or
+// past the best mismatch).  A claim that lands on a job published after the
+// claimer looked is still a valid claim of that job: the descriptor read
+// after the atomic (and a fence) is that job's, because the slot cannot be
+// republished before `done` covers it.
+__device__ __forceinline__ bool claim_valid(unsigned long long w)
 {
-    const unsigned long long w = atomicAdd(&sl->claim, 1ull);
-    __threadfence();
-    if ((w >> 32) == 0 || ((uint32_t)w & CLAIM_CLOSE))
-        return -1;
-    return (int64_t)(uint32_t)w;
+    return (w >> 32) != 0 && !((uint32_t)w & CLAIM_CLOSE);
 }
 
-// Scan (or skip) claimed chunk c of slot sl with the whole CTA, lower the
-// job's result, answer the claim.
-__device__ __noinline__ void serve_claim(const Smem S, JobSlot *sl, int64_t c)
+// Answers one valid claim: the chunk's mismatch (if any) first, then the
+// claim count, with release order so that the owner, once `done` covers
+// every claim, reads the final result.
+__device__ __forceinline__ void answer_claim(JobSlot *sl, int64_t r)
 {
-    // the slot is rewritten for every job: read it past the L1
-    const uint8_t *A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
-    const uint8_t *B = (const uint8_t *)__ldcg((const unsigned long long *)&sl->B);
-    const int64_t n = __ldcg(&sl->n), m = __ldcg(&sl->m), x = __ldcg(&sl->x), y = __ldcg(&sl->y),
-                  lim = __ldcg(&sl->lim);
-    const int64_t cs = c * (int64_t)CHUNK_BYTES;
-    // one thread decides from the job's current best, for the whole CTA
-    if (threadIdx.x == 0) {
-        *S.bc = (cs < lim && (unsigned long long)cs < *(volatile unsigned long long *)&sl->result) ? 1 : 0;
-        if (x < 0 || y < 0 || lim < 0 || x + lim > n || y + lim > m || !A || !B) {
-            // a job outside its strings: never scan it (self-check record 7)
-            *S.bc = 0;
+    if (r >= 0)
+        atomicMin(&sl->result, (unsigned long long)r);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&sl->done) : "memory");
+}
+
+// Thread 0, after a valid claim w of slot s: whether its chunk is still
+// worth scanning (inside lim and below the best mismatch found so far).
+// The job's descriptor is read into the CTA's cache once per job (the claim
+// word names the job), after a fence that orders it behind the claim.  For
+// the job already cached no fence is needed: the claim is valid, so the job
+// was open when the claim landed, and any earlier read of its result was
+// this job's (at worst too high, which only costs a scan).  A descriptor
+// outside its strings is never scanned (self-check record 7).
+__device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsigned long long w)
+{
+    const uint32_t jid = (uint32_t)(w >> 32);
+    const int64_t c = (int64_t)(uint32_t)w;
+    JobDesc *J = S.jd;
+    if (J->jid != jid || J->slot != s) {
+        __threadfence();
+        // the slot is rewritten for every job: read it past the L1
+        J->A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
+        J->B = (const uint8_t *)__ldcg((const unsigned long long *)&sl->B);
+        J->n = __ldcg(&sl->n);
+        J->m = __ldcg(&sl->m);
+        J->x = __ldcg(&sl->x);
+        J->y = __ldcg(&sl->y);
+        J->lim = __ldcg(&sl->lim);
+        J->jid = jid;
+        J->slot = s;
+        if (J->x < 0 || J->y < 0 || J->lim < 0 || J->x + J->lim > J->n || J->y + J->lim > J->m || !J->A || !J->B) {
+            J->jid = 0;
             if (S.err && atomicCAS(S.err, 0u, 7u) == 0u) {
                 S.diag[0] = 7;
                 S.diag[1] = blockIdx.x;
-                S.diag[2] = (unsigned long long)x;
-                S.diag[3] = (unsigned long long)y;
-                S.diag[4] = (unsigned long long)lim;
-                S.diag[5] = (unsigned long long)n;
-                S.diag[6] = (unsigned long long)m;
+                S.diag[2] = (unsigned long long)J->x;
+                S.diag[3] = (unsigned long long)J->y;
+                S.diag[4] = (unsigned long long)J->lim;
+                S.diag[5] = (unsigned long long)J->n;
+                S.diag[6] = (unsigned long long)J->m;
             }
+            return 0;
         }
     }
-    __syncthreads();
-    const int go = *S.bc;
-    __syncthreads();
-    if (go) {
-        const int64_t r =
-            cta_scan<4>(A, n, B, m, x, y, cs, min((int64_t)CHUNK_BYTES, lim - cs), S.smin);
-        if (threadIdx.x == 0 && r >= 0)
-            atomicMin(&sl->result, (unsigned long long)r);
-    }
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(&sl->done, 1u);
-    }
-    __syncthreads();
+    const unsigned long long best = *(volatile unsigned long long *)&sl->result;
+    const int64_t cs = c * (int64_t)CHUNK_BYTES;
+    return (cs < J->lim && (unsigned long long)cs < best) ? 1 : 0;
 }
 
-// Help one open job of any CTA (whole CTA).  Returns true if a claim was
-// made.
-__device__ bool help_one(const LvArgs &P, const Smem S)
+// The whole CTA scans claimed chunk c of the job cached in S.jd (when go)
+// and answers the claim.
+__device__ __forceinline__ void scan_claim(const Smem S, JobSlot *sl, int64_t c, int go)
+{
+    int64_t r = -1;
+    if (go) {
+        const JobDesc J = *S.jd;
+        const int64_t cs = c * (int64_t)CHUNK_BYTES;
+        const int64_t q = sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(
+            J.A, J.n, J.B, J.m, J.x + cs, J.y + cs, min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), S.smin);
+        r = q >= 0 ? cs + q : -1;
+    }
+    if (threadIdx.x == 0)
+        answer_claim(sl, r);
+}
+
+// The whole CTA claims and scans chunks of slot s's job, in order, up to
+// `budget` claims: thread 0 makes the next claim before the current chunk
+// is scanned, so that its round trip overlaps the scan.  w0: a claim made
+// already (0: make the first one here).  Stops at a void claim, or once a
+// claimed chunk lies past the end or past the best mismatch (that claim is
+// answered at once).  Returns the number of claims made and answered.
+__device__ int claim_loop(const Smem S, JobSlot *sl, int s, unsigned long long w0, int budget)
+{
+    const int tid = threadIdx.x;
+    unsigned long long w = 0; // thread 0: the current claim word
+    if (tid == 0)
+        w = w0 ? w0 : atomicAdd(&sl->claim, 1ull);
+    int made = 0;
+    for (;;) {
+        if (tid == 0) {
+            const int valid = claim_valid(w) ? 1 : 0;
+            const int go = valid ? claim_go(S, sl, s, w) : 0;
+            S.bc[0] = valid;
+            S.bc[3] = go;
+            S.bcl[0] = (int64_t)(uint32_t)w;
+            // the next claim, in flight during the scan below
+            w = (go && made + 1 < budget) ? atomicAdd(&sl->claim, 1ull) : 0ull;
+        }
+        __syncthreads();
+        const int valid = S.bc[0], go = S.bc[3];
+        const int64_t c = S.bcl[0];
+        __syncthreads();
+        if (!valid)
+            break;
+        scan_claim(S, sl, c, go);
+        made++;
+        if (!go || made >= budget)
+            break;
+    }
+    return made;
+}
+
+// Help the open jobs of other CTAs (whole CTA): up to `budget` claims on
+// one job.  Returns true if a claim was made.
+__device__ bool help_one(const LvArgs &P, const Smem S, int budget)
 {
     const int tid = threadIdx.x;
     if (tid == 0) {
-        int slot = -1;
-        long long chunk = -1;
+        int s = -1;
+        // the active bitmask (its first four words loaded together), from a
+        // CTA-dependent bit so that helpers spread over jobs
         const int nw = (gridDim.x + 63) >> 6;
-        for (int k = 0; k < nw && slot < 0; k++) {
-            const int w = (int)((blockIdx.x / 64 + k) % nw);
-            unsigned long long bits = *(volatile unsigned long long *)&P.ctl->active[w];
-            // start from a CTA-dependent bit so helpers spread over jobs
-            const int rot = blockIdx.x & 63;
-            bits = (bits >> rot) | (rot ? (bits << (64 - rot)) : 0ull);
-            while (bits && slot < 0) {
-                const int b = (__ffsll((long long)bits) - 1 + rot) & 63;
-                bits &= bits - 1;
-                const int s = w * 64 + b;
-                if (s >= (int)gridDim.x)
-                    continue;
-                JobSlot *sl = &P.slots[s];
-                // claim only when the job visibly has chunks left
-                const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
-                const uint32_t cnt = (uint32_t)w0;
-                if ((w0 >> 32) == 0 || (cnt & CLAIM_CLOSE) || cnt >= *(volatile unsigned int *)&sl->nchunks ||
-                    (unsigned long long)cnt * CHUNK_BYTES >= *(volatile unsigned long long *)&sl->result)
-                    continue;
-                const int64_t c = claim_chunk(sl);
-                if (c >= 0) {
-                    slot = s;
-                    chunk = c;
-                }
+        const volatile unsigned long long *act = P.ctl->active;
+        const unsigned long long b0 = act[0], b1 = nw > 1 ? act[1] : 0ull, b2 = nw > 2 ? act[2] : 0ull,
+                                 b3 = nw > 3 ? act[3] : 0ull;
+        const int rot = blockIdx.x & 63;
+        for (int k = 0; k < nw && s < 0; k++) {
+            const int wd = (int)((blockIdx.x / 64 + k) % nw);
+            unsigned long long b = wd == 0 ? b0 : wd == 1 ? b1 : wd == 2 ? b2 : wd == 3 ? b3 : act[wd];
+            b = (b >> rot) | (rot ? (b << (64 - rot)) : 0ull);
+            while (b && s < 0) {
+                const int j = wd * 64 + ((__ffsll((long long)b) - 1 + rot) & 63);
+                b &= b - 1;
+                if (j < (int)gridDim.x && j != (int)blockIdx.x)
+                    s = j;
             }
         }
-        S.bc[0] = slot;
-        S.bcl[0] = chunk;
+        S.bc[1] = s;
     }
     __syncthreads();
-    const int slot = S.bc[0];
-    const int64_t chunk = S.bcl[0];
+    const int s = S.bc[1];
     __syncthreads();
-    if (slot < 0)
+    if (s < 0)
         return false;
-    serve_claim(S, &P.slots[slot], chunk);
-    return true;
+    return claim_loop(S, &P.slots[s], s, 0ull, budget) > 0;
 }
 
 // The CTA's own long slide: the first mismatch of A[x..x+lim) vs B[y..).
-// The CTA scans LOCAL_STEPS steps of 64 KiB alone; what is left becomes a
-// job in the CTA's slot, claimed chunk by chunk by the CTA and by helpers;
-// the CTA then closes the job and waits for the claims still running.
-// Returns the first mismatch offset, or lim.
-__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const Pair Q, int64_t x,
-                                           int64_t y, int64_t lim)
+// The CTA scans the first local_chunks chunks alone (one sweep each, after
+// one bulk L2 prefetch of all of them); what is left becomes a job in the
+// CTA's slot (its first chunk already claimed by the CTA), whose chunks are
+// claimed in order by the CTA and by every CTA that is waiting on a
+// neighbour or has no tile; the CTA then closes the job and waits for the
+// claims still running.  Returns the first mismatch offset, or lim.
+__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const Pair Q, int64_t x0,
+                                           int64_t y0, int64_t lim0)
 {
     const int tid = threadIdx.x;
-    // what the CTA scans alone, asked of L2 at once: the steps below then
-    // wait on L2 rather than on DRAM
-    if (tid == 0) {
-        const int64_t ahead = min(lim, (int64_t)LOCAL_STEPS * CHUNK_BYTES);
-        bulk_prefetch_l2(Q.A, Q.n, x, ahead);
-        bulk_prefetch_l2(Q.B, Q.m, y, ahead);
+    const int64_t loc = min(lim0, (int64_t)max(1, P.local_chunks) * CHUNK_BYTES);
+    if (tid == 0 && loc > CHUNK_BYTES) {
+        bulk_prefetch_l2(Q.A, Q.n, x0 + CHUNK_BYTES, loc - CHUNK_BYTES);
+        bulk_prefetch_l2(Q.B, Q.m, y0 + CHUNK_BYTES, loc - CHUNK_BYTES);
     }
     int64_t off = 0;
-    for (int step = 0; step < LOCAL_STEPS && off < lim; step++) {
-        const int64_t r = cta_scan<4>(Q.A, Q.n, Q.B, Q.m, x, y, off,
-                                                 min((int64_t)CHUNK_BYTES, lim - off), S.smin);
+    for (; off < loc; off += CHUNK_BYTES) {
+        const int64_t r = sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(Q.A, Q.n, Q.B, Q.m, x0 + off, y0 + off,
+                                                                       min((int64_t)CHUNK_BYTES, lim0 - off), S.smin);
         if (r >= 0)
-            return r;
-        off += CHUNK_BYTES;
+            return off + r;
     }
-    if (off >= lim)
-        return lim;
-    // (the caller counts this as a job-slot slide: lim and the result both
-    // reach LOCAL_STEPS chunks)
+    if (off >= lim0)
+        return lim0;
+    const int64_t x = x0 + off, y = y0 + off, lim = lim0 - off;
     JobSlot *sl = &P.slots[blockIdx.x];
-    const int64_t rest = lim - off;
-    const uint32_t nch = (uint32_t)((rest + CHUNK_BYTES - 1) / CHUNK_BYTES);
+    const uint32_t nch = (uint32_t)((lim + CHUNK_BYTES - 1) / CHUNK_BYTES);
     const int word = blockIdx.x >> 6;
     const unsigned long long bit = 1ull << (blockIdx.x & 63);
     if (tid == 0) {
@@ -376,46 +431,46 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const 
         sl->B = Q.B;
         sl->n = Q.n;
         sl->m = Q.m;
-        sl->x = x + off;
-        sl->y = y + off;
-        sl->lim = rest;
-        sl->result = (unsigned long long)rest;
+        sl->x = x;
+        sl->y = y;
+        sl->lim = lim;
+        sl->result = (unsigned long long)lim;
         sl->done = 0;
         sl->nchunks = nch;
-        const uint32_t jid = (uint32_t)(sl->claim >> 32) + 1u;
+        uint32_t jid = (uint32_t)(sl->claim >> 32) + 1u;
+        jid = jid ? jid : 1u;
+        // the CTA's own cache holds the job: no read back
+        JobDesc *J = S.jd;
+        J->A = Q.A;
+        J->B = Q.B;
+        J->n = Q.n;
+        J->m = Q.m;
+        J->x = x;
+        J->y = y;
+        J->lim = lim;
+        J->jid = jid;
+        J->slot = (int)blockIdx.x;
         __threadfence();
-        atomicExch(&sl->claim, ((unsigned long long)(jid ? jid : 1u) << 32));
+        // count 1: chunk 0 is the CTA's own claim
+        atomicExch(&sl->claim, ((unsigned long long)jid << 32) | 1ull);
         atomicOr(&P.ctl->active[word], bit);
+        S.bcl[2] = (long long)(((unsigned long long)jid << 32) | 0ull);
     }
     __syncthreads();
-    for (;;) {
-        if (tid == 0) {
-            const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
-            const uint32_t cnt = (uint32_t)w0;
-            S.bcl[1] = (cnt >= nch || (unsigned long long)cnt * CHUNK_BYTES >=
-                                         *(volatile unsigned long long *)&sl->result)
-                           ? -1
-                           : claim_chunk(sl);
-        }
-        __syncthreads();
-        const int64_t c = S.bcl[1];
-        __syncthreads();
-        if (c < 0)
-            break;
-        serve_claim(S, sl, c);
-    }
+    const unsigned long long w0 = (unsigned long long)S.bcl[2];
+    __syncthreads();
+    claim_loop(S, sl, (int)blockIdx.x, w0, INT32_MAX);
     if (tid == 0) {
         atomicAnd(&P.ctl->active[word], ~bit);
         const unsigned long long w = atomicAdd(&sl->claim, (unsigned long long)CLAIM_CLOSE);
         const uint32_t nvalid = (uint32_t)w; // claims made before the close
         const uint64_t t0 = gtimer();
-        while (*(volatile unsigned int *)&sl->done < nvalid) {
+        while (ld_acquire(&sl->done) < nvalid) {
             if (gtimer() - t0 > P.spin_ns) {
                 wait_failed(P, 1, 0, nvalid, *(volatile unsigned int *)&sl->done, 0, 0);
                 break;
             }
         }
-        __threadfence();
         S.bcl[1] = (long long)*(volatile unsigned long long *)&sl->result;
     }
     __syncthreads();
@@ -502,6 +557,7 @@ __device__ Smem carve(const LvArgs &P)
     S.left = S.nL + 4;
     S.kf = S.nL + 6;
     S.nR = S.nL + 7;
+    S.jd = reinterpret_cast<JobDesc *>(p + 192);
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -528,13 +584,27 @@ struct Tile {
     int left, right; // neighbour CTA (grid index) or -1
 };
 
-__device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int gi, int c0, int h)
+// While the band is narrow (fewer than HELP_BAND diagonals per CTA), the
+// last G / help_div CTAs of a group of at least 2 * help_div CTAs hold no
+// tile: they serve the chunks of long slides as soon as they are published
+// (the rounds of a narrow band are bound by their latency, not by the
+// diagonals per CTA).
+constexpr int64_t HELP_BAND = 256;
+
+__device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int gi, int c0, int h, int help_div,
+                                          int64_t smax)
 {
     Tile T;
     T.lo_all = max(-R, -Q.n);
     T.hi_all = min(R, Q.m);
     const int64_t N = T.hi_all - T.lo_all + 1;
-    T.S = max((int64_t)h, (N + G - 1) / G);
+    int Gt = G;
+    if (help_div > 0 && G >= 2 * help_div && N < HELP_BAND * G) {
+        const int g2 = G - G / help_div;
+        if ((N + g2 - 1) / g2 <= smax) // the tiles still fit the shared memory
+            Gt = g2;
+    }
+    T.S = max((int64_t)h, (N + Gt - 1) / Gt);
     T.ntiles = (int)((N + T.S - 1) / T.S);
     T.has = gi < T.ntiles;
     T.a = T.lo_all + (int64_t)gi * T.S;
@@ -642,7 +712,7 @@ __device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const 
         const int64_t lim = S.bcl[3];
         __syncthreads();
         const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c);
-        if (lim - c > (int64_t)LOCAL_STEPS * CHUNK_BYTES && rr >= (int64_t)LOCAL_STEPS * CHUNK_BYTES)
+        if (lim - c > (int64_t)max(1, P.local_chunks) * CHUNK_BYTES) // published as a job
             C.longs++;
         if (tid < 32)
             prefetch_next(Q.A, Q.n, Q.B, Q.m, c + rr, c + rr + d);
@@ -841,12 +911,15 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
 // to k for its tile (those rounds lie in blocks that the owner of d = m - n
 // already ran at the same radius: no epoch change is needed, and its
 // neighbours have published their edges for them).
-__device__ __forceinline__ bool pair_over(const PairDesc &D, GroupCtl *gc, int64_t t)
+__device__ __forceinline__ bool pair_over_seen(const PairDesc &D, unsigned long long v, int64_t t)
 {
-    const unsigned long long v = *(volatile unsigned long long *)&gc->done_k;
     if (v == ~0ull)
         return false;
     return !D.dump || v == DONE_STOPPED || (unsigned long long)t > v;
+}
+__device__ __forceinline__ bool pair_over(const PairDesc &D, GroupCtl *gc, int64_t t)
+{
+    return pair_over_seen(D, *(volatile unsigned long long *)&gc->done_k, t);
 }
 
 // The largest epoch radius whose band [max(-R, -n), min(R, m)] fits in
@@ -905,7 +978,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         R = D.R0;
     }
     uint32_t epoch = 0;
-    Tile T = partition(Q, R, G, gi, c0, h);
+    Tile T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax);
     if (T.S > P.smax || (D.keep && R > D.keep_r)) {
         pair_stop(D, gc, ST_WIDE);
         if (tid == 0 && gi == 0 && t > 0) { // the saved state is still good
@@ -954,14 +1027,20 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             uint64_t t0 = tid == 0 ? gtimer() : 0;
             for (;;) {
                 if (tid == 0) {
+                    // the three words at once (relaxed); an acquire fence
+                    // before epoch_t is read
+                    const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
+                    const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
+                    const uint32_t eq = *(volatile uint32_t *)&gc->epoch_req;
                     int st = 0;
-                    if (*(volatile unsigned long long *)&gc->done_k != ~0ull)
+                    if (dk != ~0ull)
                         st = 1;
-                    else if (ld_acquire(&P.ctl->error) != 0)
+                    else if (er != 0)
                         st = 2;
-                    else if (ld_acquire(&gc->epoch_req) > epoch)
+                    else if (eq > epoch) {
+                        fence_acquire();
                         st = 3;
-                    else if (gtimer() - t0 > P.idle_ns) {
+                    } else if (gtimer() - t0 > P.idle_ns) {
                         wait_failed(P, 3, t, epoch, ld_acquire(&gc->epoch_req), R, T.ntiles);
                         st = 2;
                     }
@@ -981,7 +1060,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                     t = et;
                     break;
                 }
-                if (!help_one(P, S))
+                if (!help_one(P, S, 8))
                     __nanosleep(256);
             }
         }
@@ -1048,7 +1127,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             }
             t_ep = t;
             R = Rn;
-            T = partition(Q, R, G, gi, c0, h);
+            T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax);
             if (T.S > P.smax) {
                 pair_stop(D, gc, ST_WIDE);
                 return true;
@@ -1064,22 +1143,50 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             if (!T.has)
                 continue;
         }
-        // ---------------------------------------------- h rounds
         const int64_t a = T.a, b = T.b, off = a - h - 1; // smem index = d - off
-        const BlockOut bo = run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
-        C.slide += bo.slide;
-        C.mism += bo.mism;
-        C.hashq += bo.hashq;
-        C.coll += bo.coll;
-        C.longs += bo.longs;
-        C.opens += bo.opens;
-        C.tm[0] += bo.tm_round;
-        C.tm[1] += bo.tm_open;
-        const bool fin = bo.fin != 0;
-        if (fin)
-            return true;
-        t += h;
-        C.blocks++;
+        // ---------------------------------------------- blocks outside the band
+        // The band of round t' is [-t', t'].  A tile whose trapezoid (the
+        // tile and h - 1 halo diagonals per side) lies outside it for every
+        // round of a block holds minus infinity there: the block is skipped,
+        // and so is every block after it until the band can reach the
+        // trapezoid, an epoch change is due, or a sync point comes.  The tile
+        // publishes minus-infinity edges for those rounds at once (both
+        // parities: its neighbours read either) and helps long slides while
+        // its inner neighbour catches up.  The neighbours' edges of those
+        // rounds are minus infinity too (they lie further out than h - 1
+        // diagonals inside the trapezoid).
+        const int64_t dist = a > 0 ? a : (b <= 0 ? 1 - b : 0); // min |d| over the tile
+        int64_t t2 = t;
+        while (t2 + 2 * h - 2 < dist && !(t2 + h - 1 > R && R < nm) &&
+               !(can_suspend && t2 >= t_ep + P.sync_rounds))
+            t2 += h;
+        if (t2 > t) {
+            int32_t *f = frontier(S, t2 - 1);
+            for (int64_t d = a - h + tid; d < b + h; d += nt)
+                f[d - off] = NEG;
+            const int op = (int)(((t2 / h) & 1) ^ 1);
+            if (tid < h) {
+                st_cg(halo_ptr(P, blockIdx.x, op, 0) + tid, NEG);
+                st_cg(halo_ptr(P, blockIdx.x, op, 1) + tid, NEG);
+            }
+            t = t2;
+        } else {
+            // ------------------------------------------ h rounds
+            const BlockOut bo = run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
+            C.slide += bo.slide;
+            C.mism += bo.mism;
+            C.hashq += bo.hashq;
+            C.coll += bo.coll;
+            C.longs += bo.longs;
+            C.opens += bo.opens;
+            C.tm[0] += bo.tm_round;
+            C.tm[1] += bo.tm_open;
+            const bool fin = bo.fin != 0;
+            if (fin)
+                return true;
+            t += h;
+            C.blocks++;
+        }
         // ---------------------------------------------- halo exchange
         const uint64_t tw0 = clock64();
         const int parity = (int)((t / h) & 1);
@@ -1099,14 +1206,22 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         const uint64_t t0 = tid == 0 ? gtimer() : 0;
         for (;;) {
             if (tid == 0) {
+                // every word at once (relaxed loads), then an acquire fence
+                // once both neighbours' flags are up: their halo values are
+                // read after it
+                const unsigned long long lf =
+                    T.left >= 0 ? *(volatile unsigned long long *)&P.ctl->flags[T.left] : ~0ull;
+                const unsigned long long rf =
+                    T.right >= 0 ? *(volatile unsigned long long *)&P.ctl->flags[T.right] : ~0ull;
+                const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
+                const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
                 int st = 0;
-                const bool lok = T.left < 0 || ld_acquire_u64(&P.ctl->flags[T.left]) >= want;
-                const bool rok = T.right < 0 || ld_acquire_u64(&P.ctl->flags[T.right]) >= want;
-                if (lok && rok)
+                if (lf >= want && rf >= want) {
+                    fence_acquire();
                     st = 3;
-                else if (pair_over(D, gc, t))
+                } else if (pair_over_seen(D, dk, t))
                     st = 1;
-                else if (ld_acquire(&P.ctl->error) != 0)
+                else if (er != 0)
                     st = 2;
                 else if (gtimer() - t0 > P.idle_ns) {
                     wait_failed(P, 4, t, want, T.left >= 0 ? ld_acquire_u64(&P.ctl->flags[T.left]) : ~0ull,
@@ -1125,7 +1240,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 return false;
             if (st == 3)
                 break;
-            help_one(P, S);
+            help_one(P, S, 1);
         }
         int32_t *edge = frontier(S, t - 1);
         if (tid < h) {
@@ -1169,6 +1284,10 @@ __device__ __forceinline__ void flush_counters(const PairDesc &D, Counters &C, b
 __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
 {
     const Smem S = carve(P);
+    if (threadIdx.x == 0) { // no job cached (read before the first group barrier)
+        S.jd->jid = 0;
+        S.jd->slot = -1;
+    }
     const uint64_t deadline = gtimer() + P.budget_ns;
     int cls = 0;
     while (cls + 1 < P.ncls && (int)blockIdx.x >= P.cls_c0[cls + 1])
@@ -1278,29 +1397,22 @@ __global__ void lcp_query_kernel(const uint8_t *A, int64_t n, const uint8_t *B, 
 __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots)
 {
     __shared__ unsigned long long s_min;
-    __shared__ long long s_c;
+    __shared__ long long s_bcl[4];
     __shared__ int s_bc[8];
+    __shared__ JobDesc s_jd;
     Smem S{};
     S.smin = &s_min;
     S.bc = s_bc;
+    S.bcl = s_bcl;
+    S.jd = &s_jd;
+    if (threadIdx.x == 0) {
+        s_jd.jid = 0;
+        s_jd.slot = -1;
+    }
     for (int j = 0; j < nslots; j++) {
-        JobSlot *sl = &slots[(j + blockIdx.x) % nslots];
-        for (;;) {
-            if (threadIdx.x == 0) {
-                const unsigned long long w0 = *(volatile unsigned long long *)&sl->claim;
-                const uint32_t cnt = (uint32_t)w0;
-                s_c = (cnt >= *(volatile unsigned int *)&sl->nchunks ||
-                       (unsigned long long)cnt * CHUNK_BYTES >= *(volatile unsigned long long *)&sl->result)
-                          ? -1
-                          : claim_chunk(sl);
-            }
-            __syncthreads();
-            const int64_t c = s_c;
-            __syncthreads();
-            if (c < 0)
-                break;
-            serve_claim(S, sl, c);
-        }
+        const int s = (j + (int)blockIdx.x) % nslots;
+        // claims until a chunk lies past the end or the best mismatch
+        claim_loop(S, &slots[s], s, 0ull, INT32_MAX);
     }
 }
 
