@@ -202,3 +202,53 @@ def test_admission_refuses_when_slots_full(orc):
             time.sleep(0.001)
     assert res == [want, want]
     c.close()
+
+
+def test_submit_dev_strings_written_on_a_side_stream(orc):
+    """ed_submit_dev: device strings that a copy on the caller's side stream
+    is still writing when they are submitted; the engine waits for that
+    stream's work.  Mixed with host-submitted pairs; every result equals the
+    oracle's."""
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    c = ed.Context(device=0, max_inflight=64)
+    try:
+        pairs = [W.make_pair(110, 3_000_000, 40, sigma=4, extra=i) for i in range(4)]
+        pairs += [W.make_pair(111, 300_000, 9000, sigma=4)]  # wider than one CTA's band
+        want = orc.many("lv", [(p.A, p.B) for p in pairs])
+        side = torch.cuda.Stream()
+        bufs, tickets = [], []
+        for i, p in enumerate(pairs):
+            hA = torch.from_numpy(p.A).pin_memory()
+            hB = torch.from_numpy(p.B).pin_memory()
+            with torch.cuda.stream(side):
+                dA = torch.empty(p.A.size, dtype=torch.uint8, device="cuda")
+                dB = torch.empty(p.B.size, dtype=torch.uint8, device="cuda")
+                dA.copy_(hA, non_blocking=True)
+                dB.copy_(hB, non_blocking=True)
+            bufs.append((dA, dB, hA, hB))
+            if i % 2:
+                tickets.append(ed.ed_submit(c.h, p.A, p.B))
+            else:
+                tickets.append(ed.ed_submit_dev(c.h, dA, dB, stream=side))
+        got = {}
+        t0 = time.time()
+        while len(got) < len(tickets):
+            for i, t in enumerate(tickets):
+                if i not in got:
+                    st, k = ed.ed_poll(c.h, t)
+                    if st == ed.ED_OK:
+                        got[i] = k
+            assert time.time() - t0 < 120, "serving did not finish"
+            time.sleep(0.0005)
+        assert [got[i] for i in range(len(tickets))] == list(want)
+        # bad arguments: a null string with a length
+        lib = ed.load()
+        import ctypes
+
+        tk = ctypes.c_uint64()
+        assert lib.ed_submit_dev(c.h, None, 5, None, 0, ctypes.byref(tk), None) == ed.ED_EINVAL
+    finally:
+        c.close()
