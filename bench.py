@@ -257,6 +257,7 @@ def pair_record(pair, k, st, ms, peak):
             "ext_per_s": st["extensions"] / (ms / 1e3) if ms else None, "compared_bytes": cb,
             "gbs": round(gbs, 2), "frac": gbs / peak, "long_slides": st["long_slides"],
             "open_slides": st["open_slides"], "phase_ms": [round(x, 3) for x in st["phase_ms"]],
+            "build_ms": round(st["build_ms"], 4), "hash_queries": st["hash_queries"],
             "avg_lcp": st["slide_chars"] / max(1, st["extensions"])}
 
 

@@ -184,7 +184,8 @@ int ed_serve_counters(ed_ctx *ctx, uint64_t *admitted, uint64_t *completed,
  * pointers of n+1 and m+1 entries; may differ from the LCP on a hash
  * collision), 4 = hash search confirmed directly (exact), 5 and 6 = 3 and 4
  * on blocked tables (ed_prefix_hash_blocked_dev with the context's
- * hash_block b: n/b+1 and m/b+1 entries).  Synchronous. */
+ * hash_block b: n/b+1 and m/b+1 entries), 7 = 2 with each chunk staged in
+ * shared memory by bulk copies.  Synchronous. */
 int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B,
                size_t m, const int64_t *x, const int64_t *y, size_t q,
                int method, const uint64_t *TA, const uint64_t *TB,

@@ -160,6 +160,7 @@ struct ed_ctx {
     int num_sms = 0;
     int grid = 0; // CTAs of the tile kernel
     int clock_khz = 1;
+    int smem_optin = 0; // largest dynamic shared memory of one CTA
     cudaStream_t stream = nullptr;
     std::string last_err;
     size_t budget = 0;
@@ -425,7 +426,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     if ((r = ensure(ctx, ctx->gf, sizeof(int32_t) * (size_t)std::max<int64_t>(gf_total, 1))) != ED_OK ||
         (r = ensure(ctx, ctx->ctl, sizeof(LaunchCtl))) != ED_OK ||
         (r = ensure(ctx, ctx->gctl, sizeof(GroupCtl) * ngroups)) != ED_OK ||
-        (r = ensure(ctx, ctx->slots, sizeof(JobSlot) * grid)) != ED_OK ||
+        (r = ensure(ctx, ctx->slots, sizeof(JobSlot) * grid * JOB_RING)) != ED_OK ||
         (r = ensure(ctx, ctx->halo, sizeof(int32_t) * (size_t)grid * 4 * HMAX)) != ED_OK ||
         (r = ensure(ctx, ctx->pdesc, sizeof(PairDesc) * np)) != ED_OK ||
         (r = ensure(ctx, ctx->res, sizeof(unsigned long long) * R_COUNT * np)) != ED_OK)
@@ -479,10 +480,12 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.sync_rounds = 16 * h;
     P.help_div = 8;
     P.local_chunks = 1;
+    // bulk-copy staging of long-slide chunks when the tiles leave room for it
+    P.stage = lv_tiles_smem_bytes((int)smax, h, 1) <= (size_t)ctx->smem_optin ? 1 : 0;
     CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->ctl.p, 0, sizeof(LaunchCtl), s));
     CK(cudaMemsetAsync(ctx->gctl.p, 0, sizeof(GroupCtl) * ngroups, s));
-    CK(cudaMemsetAsync(ctx->slots.p, 0, sizeof(JobSlot) * grid, s));
+    CK(cudaMemsetAsync(ctx->slots.p, 0, sizeof(JobSlot) * grid * JOB_RING, s));
     CK(cudaMemsetAsync(ctx->res.p, 0, sizeof(unsigned long long) * R_COUNT * np, s));
     CK(cudaEventRecord(ctx->ev0, s));
     CK(launch_lv_tiles(P, grid, s));
@@ -687,6 +690,7 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
     c->device = dev;
     CK(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     CK(cudaDeviceGetAttribute(&c->clock_khz, cudaDevAttrClockRate, dev));
+    CK(cudaDeviceGetAttribute(&c->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     c->clock_khz = std::max(c->clock_khz, 1);
     size_t fr = 0, tot = 0;
     CK(cudaMemGetInfo(&fr, &tot));
@@ -953,9 +957,9 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
                const int64_t *y, size_t q, int method, const uint64_t *TA, const uint64_t *TB, int64_t *out,
                void *stream)
 {
-    if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 6 || bad_len(n) || bad_len(m))
+    if (!ctx || (q && (!x || !y || !out)) || method < 0 || method > 7 || bad_len(n) || bad_len(m))
         return ED_EINVAL;
-    if (method >= 3 && (!TA || !TB))
+    if (method >= 3 && method <= 6 && (!TA || !TB))
         return ED_EINVAL;
     for (size_t i = 0; i < q; i++)
         if (x[i] < 0 || y[i] < 0 || x[i] > (int64_t)n || y[i] > (int64_t)m)
@@ -966,7 +970,7 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
         return ED_OK;
     cudaStream_t s = (cudaStream_t)stream;
     int r;
-    if (method == 2) {
+    if (method == 2 || method == 7) {
         if ((r = ensure(ctx, ctx->slots, sizeof(JobSlot) * q)) != ED_OK)
             return r;
         std::vector<JobSlot> it(q);
@@ -985,7 +989,7 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
             j.m = (long long)m;
         }
         CK(cudaMemcpyAsync(ctx->slots.p, it.data(), sizeof(JobSlot) * q, cudaMemcpyHostToDevice, s));
-        CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, nullptr, nullptr, (int64_t)q, 2, nullptr,
+        CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, nullptr, nullptr, (int64_t)q, method, nullptr,
                               nullptr, (JobSlot *)ctx->slots.p, ctx->grid, s));
         CK(cudaMemcpyAsync(it.data(), ctx->slots.p, sizeof(JobSlot) * q, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));

@@ -517,6 +517,176 @@ __device__ __forceinline__ int64_t sweep_scan(const uint8_t *A, int64_t n, const
     return -1;
 }
 
+// ------------------------------------------------------- bulk copies
+// Shared-memory address of a generic pointer into shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// Orders an mbarrier's initialisation before its use by the bulk-copy
+// (async) proxy.
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// The calling thread's arrival on bar, announcing `bytes` of bulk copies
+// that will complete on it.
+__device__ __forceinline__ void mbar_arrive_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// A bulk copy of `bytes` (a multiple of 16; both addresses 16-byte aligned)
+// from global memory into this CTA's shared memory, completing on bar.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    uint64_t g;
+    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(src));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+// True once bar's phase `parity` has completed.
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+// Orders this thread's earlier shared-memory reads before later bulk copies
+// (async proxy) into the same bytes.
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Shared-memory staging of one chunk for stage_scan: the A side (chunk +
+// 16 bytes), the B side (chunk + 32 bytes), the mbarrier the copies
+// complete on, and the phase to wait for next.
+struct Stage {
+    unsigned char *a, *b;
+    uint64_t *bar;
+    uint32_t *phase;
+};
+template <int CH>
+constexpr size_t stage_bytes()
+{
+    return (size_t)CH + 16 + (size_t)CH + 32 + 16 + 16;
+}
+
+// The calling CTA compares A[x0 .. x0+len) with B[y0 .. y0+len) for
+// len <= CH (the chunk size) and returns the first mismatching offset, or
+// -1 if all are equal; needs x0 + len <= n and y0 + len <= m.  Thread 0
+// copies both windows into the stage by two bulk copies (aligned 16-byte
+// blocks, clipped to the blocks that overlap each string); every thread
+// waits on the stage's mbarrier, bounded by spin_ns (on expiry: *err set,
+// then one more bounded wait for the copies, and -2 returned), then
+// compares its 16-byte blocks of A with the B bytes paired with them (two
+// aligned 16-byte reads and a byte shift).  Bytes copied from outside a
+// string, or not copied at all, pair only with offsets outside [0, len).
+// Every thread must call it; s_min is a shared 64-bit scratch word.
+template <int CH>
+__device__ __noinline__ int64_t stage_scan(const Stage T, const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
+                                           int64_t x0, int64_t y0, int64_t len, unsigned long long *s_min,
+                                           uint64_t spin_ns, uint32_t *err)
+{
+    const int tid = threadIdx.x;
+    const uintptr_t pa = (uintptr_t)(A + x0);
+    const uint32_t sa = (uint32_t)(pa & 15);
+    const uintptr_t a0 = pa - sa;
+    const uintptr_t pbs = (uintptr_t)(B + y0) - sa; // B address paired with a0
+    const uint32_t qb = (uint32_t)(pbs & 15);
+    const uintptr_t b0 = pbs - qb;
+    const int64_t nblk = (sa + len + 15) >> 4; // A blocks holding offsets [0, len)
+    const uint32_t parity = *T.phase;
+    if (tid == 0) {
+        *s_min = ~0ull;
+        // A: blocks a0 .. a0 + 16*nblk, clipped to the last block of A
+        const uintptr_t aend = (((uintptr_t)A + (uintptr_t)n - 1) & ~(uintptr_t)15) + 16;
+        const uint32_t la = (uint32_t)(min(a0 + 16 * (uintptr_t)nblk, aend) - a0);
+        // B: blocks b0 .. b0 + 16*(nblk+1), clipped to the blocks of B
+        const uintptr_t bfirst = (uintptr_t)B & ~(uintptr_t)15;
+        const uintptr_t bend = (((uintptr_t)B + (uintptr_t)m - 1) & ~(uintptr_t)15) + 16;
+        const uintptr_t bs = max(b0, bfirst);
+        const uintptr_t be = min(b0 + 16 * (uintptr_t)(nblk + 1), bend);
+        const uint32_t lb = (uint32_t)(be - bs);
+        mbar_arrive_tx(T.bar, la + lb);
+        bulk_g2s(T.a, (const void *)a0, la, T.bar);
+        bulk_g2s(T.b + (bs - b0), (const void *)bs, lb, T.bar);
+    }
+    // wait for both copies (bounded)
+    bool ok = mbar_test(T.bar, parity);
+    if (!ok) {
+        const uint64_t t0 = gtimer();
+        while (!(ok = mbar_test(T.bar, parity))) {
+            if (gtimer() - t0 > spin_ns)
+                break;
+        }
+    }
+    if (!__syncthreads_and(ok)) {
+        // record, then give the copies one more bounded wait before the
+        // stage may be touched again
+        if (tid == 0) {
+            atomicCAS(err, 0u, 4u);
+            const uint64_t t1 = gtimer();
+            while (!mbar_test(T.bar, parity) && gtimer() - t1 < spin_ns) {
+            }
+            *T.phase = parity ^ 1u;
+        }
+        __syncthreads();
+        return -2;
+    }
+    int64_t best = -1;
+    for (int64_t j = tid; j < nblk && best < 0; j += blockDim.x) {
+        const uint4 va = *reinterpret_cast<const uint4 *>(T.a + 16 * j);
+        const uint4 lo = *reinterpret_cast<const uint4 *>(T.b + 16 * j);
+        const uint4 hi = *reinterpret_cast<const uint4 *>(T.b + 16 * j + 16);
+        const uint4 bs = shift_bytes(lo, hi, qb);
+        const int64_t o0 = 16 * j - (int64_t)sa;
+        const int lo_i = o0 < 0 ? (int)-o0 : 0;
+        const int64_t hi64 = len - o0;
+        const int hi_i = hi64 >= 16 ? 16 : (hi64 <= 0 ? 0 : (int)hi64);
+        if (lo_i < hi_i) {
+            uint64_t d0 = ((uint64_t)(va.y ^ bs.y) << 32) | (uint64_t)(va.x ^ bs.x);
+            uint64_t d1 = ((uint64_t)(va.w ^ bs.w) << 32) | (uint64_t)(va.z ^ bs.z);
+            const uint64_t k0lo = lo_i >= 8 ? 0ull : (~0ull << (8 * lo_i));
+            const uint64_t k1lo = lo_i <= 8 ? ~0ull : (~0ull << (8 * (lo_i - 8)));
+            const uint64_t k0hi = hi_i >= 8 ? ~0ull : ((1ull << (8 * hi_i)) - 1ull);
+            const uint64_t k1hi = hi_i <= 8 ? 0ull : (hi_i >= 16 ? ~0ull : ((1ull << (8 * (hi_i - 8))) - 1ull));
+            d0 &= k0lo & k0hi;
+            d1 &= k1lo & k1hi;
+            if (d0)
+                best = o0 + ((__ffsll((long long)d0) - 1) >> 3);
+            else if (d1)
+                best = o0 + 8 + ((__ffsll((long long)d1) - 1) >> 3);
+        }
+    }
+    // the stage is read: the next copies may overwrite it after this barrier
+    fence_proxy_async_smem();
+    const int any = __syncthreads_or(best >= 0);
+    if (tid == 0)
+        *T.phase = parity ^ 1u;
+    if (any) {
+        if (best >= 0)
+            atomicMin(s_min, (unsigned long long)best);
+        __syncthreads();
+        const int64_t r = (int64_t)*s_min;
+        __syncthreads(); // read by all before the next call resets it
+        return r;
+    }
+    __syncthreads(); // the phase update is seen by all before the next call
+    return -1;
+}
+
 // ------------------------------------------------------- mod 2^61 - 1
 // a * b mod q for a, b < q: the 122-bit product hi:lo splits as
 // (hi << 3 | lo >> 61) * 2^61 + (lo & q), and 2^61 = 1 (mod q).

@@ -21,12 +21,15 @@ constexpr int MAX_CLS = 12;        // group-size classes of one tile launch
 // done_k of a pair that ended without a distance (status in its R_STATUS)
 constexpr unsigned long long DONE_STOPPED = ~0ull - 1;
 
-// A long slide open for help.  Each CTA owns one slot.  `claim` packs the
-// job id (high 32 bits) and the count of claims made (low 32 bits): every
-// atomicAdd of 1 claims the next chunk (CHUNK_BYTES of each string), and the owner closes the job
-// by adding a high bit to the count (the protocol is in lv_tiles.cu);
-// `result` (first mismatch offset, starts at lim) falls by atomicMin;
-// `done` counts answered claims.
+// A long slide open for help.  Each CTA owns JOB_RING slots, used in turn.
+// `claim` packs the job id (high 32 bits) and the count of claims made (low
+// 32 bits): every atomicAdd of 1 claims the next chunk (CHUNK_BYTES of each
+// string), and the owner closes the job by adding a high bit to the count
+// (the protocol is in lv_tiles.cu); `result` (first mismatch offset, starts
+// at lim) falls by atomicMin; `bits` marks the chunks scanned; `done` counts
+// answered claims (a slot is reused once it covers every claim).
+constexpr int JOB_RING = 2;
+constexpr int JOB_MAX_CHUNKS = 4096; // chunks of one job; longer slides are cut
 struct __align__(128) JobSlot {
     unsigned long long claim;
     unsigned long long result;
@@ -34,6 +37,9 @@ struct __align__(128) JobSlot {
     unsigned int done, nchunks;
     const uint8_t *A, *B; // the strings compared (any pair of the launch)
     long long n, m;
+    unsigned int nvalid;  // claims made before the close (the owner's record)
+    unsigned int pad;
+    unsigned long long bits[JOB_MAX_CHUNKS / 64];
 };
 
 // One pair of a tile launch.
@@ -73,7 +79,7 @@ struct __align__(64) LaunchCtl {
     // where the first failed wait gave up: site, CTA, round, awaited value,
     // values seen, done_k
     unsigned long long diag[8];
-    unsigned long long active[(MAX_GRID + 63) / 64]; // job slots open for help
+    unsigned long long active[(MAX_GRID * JOB_RING + 63) / 64]; // job slots open for help
     // per CTA: (pair iteration << 32) | first round not yet published
     unsigned long long flags[MAX_GRID];
 };
@@ -112,7 +118,7 @@ struct LvArgs {
     int64_t cls_gf[MAX_CLS];
     GroupCtl *gctl;
     LaunchCtl *ctl;
-    JobSlot *slots;       // gridDim.x slots
+    JobSlot *slots;       // gridDim.x * JOB_RING slots (CTA c owns c * JOB_RING ..)
     int32_t *halo;        // [gridDim.x][2 parity][2 sides][HMAX]
     int32_t *gf;
     int32_t kcap;         // round cap (largest epoch radius)
@@ -135,9 +141,11 @@ struct LvArgs {
     int32_t help_div;
     // chunks of a long slide its CTA scans alone before publishing the rest
     int32_t local_chunks;
+    // 1: each CTA stages a chunk's bytes in shared memory by bulk copies
+    int32_t stage;
 };
 
-size_t lv_tiles_smem_bytes(int smax, int h);
+size_t lv_tiles_smem_bytes(int smax, int h, int stage);
 cudaError_t launch_lv_tiles(const LvArgs &P, int grid, cudaStream_t s);
 
 // ---------------------------------------------------------------- batch

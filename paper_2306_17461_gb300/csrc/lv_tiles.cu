@@ -218,6 +218,18 @@ struct JobDesc {
 };
 static_assert(sizeof(JobDesc) <= 64, "the job cache fills bytes 192..255 of the smem header");
 
+// The parts of a chunk's staging at p (128-byte aligned): A side, B side,
+// mbarrier, phase word.
+__device__ __forceinline__ Stage stage_of(unsigned char *p)
+{
+    Stage T;
+    T.a = p;
+    T.b = p + CHUNK_BYTES + 16;
+    T.bar = reinterpret_cast<uint64_t *>(T.b + CHUNK_BYTES + 32);
+    T.phase = reinterpret_cast<uint32_t *>(T.bar + 1);
+    return T;
+}
+
 // Kept in registers: every function takes it by value (no address taken,
 // no array member indexed at run time).
 struct Smem {
@@ -235,6 +247,8 @@ struct Smem {
     long long *bcl;     // 4 broadcast 64-bit words
     unsigned long long *smin;
     JobDesc *jd;        // the job last claimed from
+    int *jring;         // the CTA's next job slot (0 .. JOB_RING-1)
+    unsigned char *stg; // bulk-copy staging of one chunk (null: none), see stage_of
     int lcap;
     uint32_t *err;             // launch status word (self-check records)
     unsigned long long *diag;
@@ -254,14 +268,25 @@ __device__ __forceinline__ bool claim_valid(unsigned long long w)
     return (w >> 32) != 0 && !((uint32_t)w & CLAIM_CLOSE);
 }
 
-// Answers one valid claim: the chunk's mismatch (if any) first, then the
-// claim count, with release order so that the owner, once `done` covers
-// every claim, reads the final result.
-__device__ __forceinline__ void answer_claim(JobSlot *sl, int64_t r)
+// Answers one valid claim of chunk c: marks the chunk answered and counts
+// the answer.  A chunk with a mismatch lowers the result first and marks
+// itself with release order, so that a reader that sees the mark (acquire)
+// sees the lowered result; a chunk without one wrote nothing else, and its
+// mark and count need no order and do not make the thread wait.  (A slot is
+// reused only once every mark and count of its claims is seen.)
+__device__ __forceinline__ void answer_claim(JobSlot *sl, int64_t c, int64_t r)
 {
-    if (r >= 0)
+    const bool mark = c >= 0 && c < JOB_MAX_CHUNKS;
+    unsigned long long *bw = &sl->bits[mark ? c >> 6 : 0];
+    const unsigned long long bit = 1ull << (c & 63);
+    if (r >= 0) {
         atomicMin(&sl->result, (unsigned long long)r);
-    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&sl->done) : "memory");
+        if (mark)
+            asm volatile("red.release.gpu.global.or.b64 [%0], %1;" ::"l"(bw), "l"(bit) : "memory");
+    } else if (mark) {
+        asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(bw), "l"(bit) : "memory");
+    }
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&sl->done) : "memory");
 }
 
 // Thread 0, after a valid claim w of slot s: whether its chunk is still
@@ -272,12 +297,15 @@ __device__ __forceinline__ void answer_claim(JobSlot *sl, int64_t r)
 // was open when the claim landed, and any earlier read of its result was
 // this job's (at worst too high, which only costs a scan).  A descriptor
 // outside its strings is never scanned (self-check record 7).
-__device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsigned long long w)
+__device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsigned long long w,
+                                        unsigned long long best = ~0ull)
 {
     const uint32_t jid = (uint32_t)(w >> 32);
     const int64_t c = (int64_t)(uint32_t)w;
     JobDesc *J = S.jd;
+    bool fresh = false;
     if (J->jid != jid || J->slot != s) {
+        fresh = true;
         __threadfence();
         // the slot is rewritten for every job: read it past the L1
         J->A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
@@ -303,59 +331,99 @@ __device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsign
             return 0;
         }
     }
-    const unsigned long long best = *(volatile unsigned long long *)&sl->result;
+    // best: read along with the claim (any read made while one of this CTA's
+    // claims on the job was unanswered is this job's); for a job just read
+    // in, after the fence
+    if (fresh || best == ~0ull)
+        best = *(volatile unsigned long long *)&sl->result;
     const int64_t cs = c * (int64_t)CHUNK_BYTES;
     return (cs < J->lim && (unsigned long long)cs < best) ? 1 : 0;
 }
 
+// The first mismatch of A[x0..x0+len) vs B[y0..) (len <= CHUNK_BYTES), or
+// -1: by bulk copies into the CTA's stage when it has one, else by one
+// register sweep.  Whole CTA.  (A stage wait that gave up has set the launch
+// status; the chunk then counts as equal and the launch reports the timeout.)
+__device__ __forceinline__ int64_t chunk_scan(const LvArgs &P, const Smem S, const uint8_t *A, int64_t n,
+                                              const uint8_t *B, int64_t m, int64_t x0, int64_t y0, int64_t len)
+{
+    if (S.stg) {
+        const int64_t r = stage_scan<CHUNK_BYTES>(stage_of(S.stg), A, n, B, m, x0, y0, len, S.smin, P.spin_ns, S.err);
+        return r >= 0 ? r : -1;
+    }
+    return sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(A, n, B, m, x0, y0, len, S.smin);
+}
+
 // The whole CTA scans claimed chunk c of the job cached in S.jd (when go)
 // and answers the claim.
-__device__ __forceinline__ void scan_claim(const Smem S, JobSlot *sl, int64_t c, int go)
+__device__ __forceinline__ void scan_claim(const LvArgs &P, const Smem S, JobSlot *sl, int64_t c, int go)
 {
     int64_t r = -1;
     if (go) {
         const JobDesc J = *S.jd;
         const int64_t cs = c * (int64_t)CHUNK_BYTES;
-        const int64_t q = sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(
-            J.A, J.n, J.B, J.m, J.x + cs, J.y + cs, min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), S.smin);
+        const int64_t q = chunk_scan(P, S, J.A, J.n, J.B, J.m, J.x + cs, J.y + cs,
+                                     min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs));
         r = q >= 0 ? cs + q : -1;
     }
     if (threadIdx.x == 0)
-        answer_claim(sl, r);
+        answer_claim(sl, c, r);
 }
+
+// What ends a CTA's helping early: both neighbours' flags (null: none) at
+// `want` or beyond, i.e. the CTA's own next block can start.
+struct Wake {
+    const unsigned long long *lf, *rf;
+    unsigned long long want;
+};
 
 // The whole CTA claims and scans chunks of slot s's job, in order, up to
 // `budget` claims: thread 0 makes the next claim before the current chunk
 // is scanned, so that its round trip overlaps the scan.  w0: a claim made
-// already (0: make the first one here).  Stops at a void claim, or once a
+// already (0: make the first one here).  Stops at a void claim, once a
 // claimed chunk lies past the end or past the best mismatch (that claim is
-// answered at once).  Returns the number of claims made and answered.
-__device__ int claim_loop(const Smem S, JobSlot *sl, int s, unsigned long long w0, int budget)
+// answered at once), or, with a Wake, once the CTA's neighbours are ready
+// (checked along with each claim).  Returns the number of claims made and
+// answered.
+__device__ int claim_loop(const LvArgs &P, const Smem S, JobSlot *sl, int s, unsigned long long w0, int budget,
+                          const Wake *wake = nullptr)
 {
     const int tid = threadIdx.x;
-    unsigned long long w = 0; // thread 0: the current claim word
+    unsigned long long w = 0;     // thread 0: the current claim word
+    unsigned long long best = ~0ull; // thread 0: the result read with it (~0: none)
     if (tid == 0)
         w = w0 ? w0 : atomicAdd(&sl->claim, 1ull);
     int made = 0;
     for (;;) {
         if (tid == 0) {
+            bool ready = false;
+            if (wake) {
+                const unsigned long long lf = wake->lf ? *(volatile const unsigned long long *)wake->lf : ~0ull;
+                const unsigned long long rf = wake->rf ? *(volatile const unsigned long long *)wake->rf : ~0ull;
+                ready = lf >= wake->want && rf >= wake->want;
+            }
             const int valid = claim_valid(w) ? 1 : 0;
-            const int go = valid ? claim_go(S, sl, s, w) : 0;
+            const int go = valid ? claim_go(S, sl, s, w, best) : 0;
             S.bc[0] = valid;
             S.bc[3] = go;
             S.bcl[0] = (int64_t)(uint32_t)w;
-            // the next claim, in flight during the scan below
-            w = (go && made + 1 < budget) ? atomicAdd(&sl->claim, 1ull) : 0ull;
+            // the next claim and a look at the result, both in flight during
+            // the scan below (this claim is still unanswered: the job cannot
+            // change meanwhile)
+            const bool next = go && !ready && made + 1 < budget;
+            w = next ? atomicAdd(&sl->claim, 1ull) : 0ull;
+            best = next ? *(volatile unsigned long long *)&sl->result : ~0ull;
+            S.bc[4] = next;
         }
         __syncthreads();
-        const int valid = S.bc[0], go = S.bc[3];
+        const int valid = S.bc[0], go = S.bc[3], more = S.bc[4];
         const int64_t c = S.bcl[0];
         __syncthreads();
         if (!valid)
             break;
-        scan_claim(S, sl, c, go);
+        scan_claim(P, S, sl, c, go);
         made++;
-        if (!go || made >= budget)
+        if (!more)
             break;
     }
     return made;
@@ -363,26 +431,36 @@ __device__ int claim_loop(const Smem S, JobSlot *sl, int s, unsigned long long w
 
 // Help the open jobs of other CTAs (whole CTA): up to `budget` claims on
 // one job.  Returns true if a claim was made.
-__device__ bool help_one(const LvArgs &P, const Smem S, int budget)
+__device__ bool help_one(const LvArgs &P, const Smem S, int budget, const Wake *wake = nullptr)
 {
     const int tid = threadIdx.x;
     if (tid == 0) {
         int s = -1;
-        // the active bitmask (its first four words loaded together), from a
-        // CTA-dependent bit so that helpers spread over jobs
-        const int nw = (gridDim.x + 63) >> 6;
+        // the active bitmask over the job slots (its first eight words loaded
+        // together), from a CTA-dependent bit so that helpers spread over jobs
+        const int nslot = (int)gridDim.x * JOB_RING;
+        const int nw = (nslot + 63) >> 6;
         const volatile unsigned long long *act = P.ctl->active;
-        const unsigned long long b0 = act[0], b1 = nw > 1 ? act[1] : 0ull, b2 = nw > 2 ? act[2] : 0ull,
-                                 b3 = nw > 3 ? act[3] : 0ull;
+        unsigned long long b[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            b[k] = k < nw ? act[k] : 0ull;
         const int rot = blockIdx.x & 63;
+        const int w0 = (int)(((int)blockIdx.x * JOB_RING / 64) % nw);
         for (int k = 0; k < nw && s < 0; k++) {
-            const int wd = (int)((blockIdx.x / 64 + k) % nw);
-            unsigned long long b = wd == 0 ? b0 : wd == 1 ? b1 : wd == 2 ? b2 : wd == 3 ? b3 : act[wd];
-            b = (b >> rot) | (rot ? (b << (64 - rot)) : 0ull);
-            while (b && s < 0) {
-                const int j = wd * 64 + ((__ffsll((long long)b) - 1 + rot) & 63);
-                b &= b - 1;
-                if (j < (int)gridDim.x && j != (int)blockIdx.x)
+            const int wd = (w0 + k) % nw;
+            unsigned long long v = 0ull;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                if (wd == q)
+                    v = b[q];
+            if (wd >= 8)
+                v = act[wd];
+            v = (v >> rot) | (rot ? (v << (64 - rot)) : 0ull);
+            while (v && s < 0) {
+                const int j = wd * 64 + ((__ffsll((long long)v) - 1 + rot) & 63);
+                v &= v - 1;
+                if (j < nslot && j / JOB_RING != (int)blockIdx.x)
                     s = j;
             }
         }
@@ -393,40 +471,62 @@ __device__ bool help_one(const LvArgs &P, const Smem S, int budget)
     __syncthreads();
     if (s < 0)
         return false;
-    return claim_loop(S, &P.slots[s], s, 0ull, budget) > 0;
+    return claim_loop(P, S, &P.slots[s], s, 0ull, budget, wake) > 0;
 }
 
-// The CTA's own long slide: the first mismatch of A[x..x+lim) vs B[y..).
-// The CTA scans the first local_chunks chunks alone (one sweep each, after
-// one bulk L2 prefetch of all of them); what is left becomes a job in the
-// CTA's slot (its first chunk already claimed by the CTA), whose chunks are
+// One job of the CTA's long slide (whole CTA): the first mismatch of
+// A[x..x+lim) vs B[y..), lim <= JOB_MAX_CHUNKS chunks, or lim.  The job goes
+// into the CTA's next ring slot (once every claim of the job that slot held
+// before is answered), its chunk 0 claimed by the CTA itself; the chunks are
 // claimed in order by the CTA and by every CTA that is waiting on a
-// neighbour or has no tile; the CTA then closes the job and waits for the
-// claims still running.  Returns the first mismatch offset, or lim.
-__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const Pair Q, int64_t x0,
-                                           int64_t y0, int64_t lim0)
+// neighbour or has no tile.  The CTA watches the job: its answer is final
+// once every chunk up to the one holding the best mismatch (or every chunk)
+// is marked answered; the CTA then closes the job and returns without
+// waiting for claims past that chunk.
+__device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pair Q, int64_t x, int64_t y,
+                                        int64_t lim)
 {
-    const int tid = threadIdx.x;
-    const int64_t loc = min(lim0, (int64_t)max(1, P.local_chunks) * CHUNK_BYTES);
-    if (tid == 0 && loc > CHUNK_BYTES) {
-        bulk_prefetch_l2(Q.A, Q.n, x0 + CHUNK_BYTES, loc - CHUNK_BYTES);
-        bulk_prefetch_l2(Q.B, Q.m, y0 + CHUNK_BYTES, loc - CHUNK_BYTES);
-    }
-    int64_t off = 0;
-    for (; off < loc; off += CHUNK_BYTES) {
-        const int64_t r = sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(Q.A, Q.n, Q.B, Q.m, x0 + off, y0 + off,
-                                                                       min((int64_t)CHUNK_BYTES, lim0 - off), S.smin);
-        if (r >= 0)
-            return off + r;
-    }
-    if (off >= lim0)
-        return lim0;
-    const int64_t x = x0 + off, y = y0 + off, lim = lim0 - off;
-    JobSlot *sl = &P.slots[blockIdx.x];
+    const int tid = threadIdx.x, lane = tid & 31;
     const uint32_t nch = (uint32_t)((lim + CHUNK_BYTES - 1) / CHUNK_BYTES);
-    const int word = blockIdx.x >> 6;
-    const unsigned long long bit = 1ull << (blockIdx.x & 63);
+    const int ring = *S.jring;
+    const int sidx = (int)blockIdx.x * JOB_RING + ring;
+    JobSlot *sl = &P.slots[sidx];
+    const int word = sidx >> 6;
+    const unsigned long long bit = 1ull << (sidx & 63);
+    // ------------------------------------------------ reuse of the slot
+    if (tid < 32) {
+        // every claim of the slot's last job answered, and its marks seen
+        // (the claims made before its close; 0 for a slot not used yet)
+        const uint32_t cnt = sl->nvalid;
+        const uint32_t need = min(cnt, (uint32_t)JOB_MAX_CHUNKS);
+        const uint64_t t0 = gtimer();
+        for (;;) {
+            bool ok = true;
+            for (uint32_t w = lane; w * 64 < need; w += 32) {
+                const uint32_t hi = min(need - w * 64, 64u);
+                const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
+                ok &= ((*(volatile unsigned long long *)&sl->bits[w]) & want) == want;
+            }
+            ok = __all_sync(0xffffffffu, ok);
+            ok = ok && *(volatile unsigned int *)&sl->done >= cnt;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (ok)
+                break;
+            if (gtimer() - t0 > P.spin_ns) {
+                if (lane == 0)
+                    wait_failed(P, 6, 0, cnt, *(volatile unsigned int *)&sl->done, sidx, 0);
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t w = tid; w * 64 < nch; w += blockDim.x)
+        sl->bits[w] = 0ull;
+    __threadfence();
+    __syncthreads();
+    // ------------------------------------------------ publish
     if (tid == 0) {
+        *S.jring = (ring + 1) % JOB_RING;
         sl->A = Q.A;
         sl->B = Q.B;
         sl->n = Q.n;
@@ -449,34 +549,98 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const 
         J->y = y;
         J->lim = lim;
         J->jid = jid;
-        J->slot = (int)blockIdx.x;
-        __threadfence();
-        // count 1: chunk 0 is the CTA's own claim
-        atomicExch(&sl->claim, ((unsigned long long)jid << 32) | 1ull);
-        atomicOr(&P.ctl->active[word], bit);
-        S.bcl[2] = (long long)(((unsigned long long)jid << 32) | 0ull);
+        J->slot = sidx;
+        // count 1: chunk 0 is the CTA's own claim; the descriptor and the
+        // cleared marks are visible before the claim word (release), which
+        // opens the job
+        st_release_u64(&sl->claim, ((unsigned long long)jid << 32) | 1ull);
+        asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(&P.ctl->active[word]), "l"(bit) : "memory");
+        S.bcl[2] = (long long)((unsigned long long)jid << 32);
     }
     __syncthreads();
     const unsigned long long w0 = (unsigned long long)S.bcl[2];
     __syncthreads();
-    claim_loop(S, sl, (int)blockIdx.x, w0, INT32_MAX);
-    if (tid == 0) {
-        atomicAnd(&P.ctl->active[word], ~bit);
-        const unsigned long long w = atomicAdd(&sl->claim, (unsigned long long)CLAIM_CLOSE);
-        const uint32_t nvalid = (uint32_t)w; // claims made before the close
-        const uint64_t t0 = gtimer();
-        while (ld_acquire(&sl->done) < nvalid) {
-            if (gtimer() - t0 > P.spin_ns) {
-                wait_failed(P, 1, 0, nvalid, *(volatile unsigned int *)&sl->done, 0, 0);
-                break;
+    claim_loop(P, S, sl, sidx, w0, 1); // chunk 0
+    // ------------------------------------------------ watch
+    // warp 0 looks at the marks (acquire), then at the result and the claim
+    // count: final once every chunk up to the one holding the best mismatch
+    // is answered; with no claim made since the last look (no helper at
+    // hand), the CTA scans a chunk itself
+    uint32_t last = 1;
+    for (;;) {
+        if (tid < 32) {
+            const unsigned long long best0 = *(volatile unsigned long long *)&sl->result;
+            const uint32_t cs = best0 < (unsigned long long)lim ? (uint32_t)(best0 / CHUNK_BYTES) : nch - 1;
+            const uint32_t need = min(cs + 1, nch);
+            bool ok = true;
+            for (uint32_t w = lane; w * 64 < need; w += 32) {
+                const uint32_t hi = min(need - w * 64, 64u);
+                const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
+                ok &= ((*(volatile unsigned long long *)&sl->bits[w]) & want) == want;
+            }
+            fence_acquire();
+            ok = __all_sync(0xffffffffu, ok);
+            if (lane == 0) {
+                // the result after the marks: every mismatch of a chunk seen
+                // answered is in it
+                const unsigned long long best = *(volatile unsigned long long *)&sl->result;
+                const uint32_t cnt = (uint32_t)*(volatile unsigned long long *)&sl->claim & ~CLAIM_CLOSE;
+                int act = 0; // 0 look again, 1 scan a chunk, 2 final
+                if (ok && best <= best0)
+                    act = 2;
+                else if (cnt == last && cnt < nch)
+                    act = 1;
+                last = cnt;
+                S.bc[5] = act;
+                S.bcl[1] = (long long)best;
             }
         }
-        S.bcl[1] = (long long)*(volatile unsigned long long *)&sl->result;
+        __syncthreads();
+        const int act = S.bc[5];
+        const int64_t best = S.bcl[1];
+        __syncthreads();
+        if (act == 2) {
+            if (tid == 0) {
+                asm volatile("red.relaxed.gpu.global.and.b64 [%0], %1;" ::"l"(&P.ctl->active[word]), "l"(~bit)
+                             : "memory");
+                // claims after the close are void (never answered, never marked)
+                sl->nvalid = (uint32_t)atomicAdd(&sl->claim, (unsigned long long)CLAIM_CLOSE);
+            }
+            return best;
+        }
+        if (act == 1)
+            claim_loop(P, S, sl, sidx, 0ull, 1);
     }
-    __syncthreads();
-    const int64_t r = S.bcl[1];
-    __syncthreads();
-    return off + r;
+}
+
+// The CTA's own long slide: the first mismatch of A[x..x+lim) vs B[y..).
+// The CTA scans the first local_chunks chunks alone (after one bulk L2
+// prefetch of all of them); the rest goes to jobs of at most JOB_MAX_CHUNKS
+// chunks each, helped by other CTAs.  Returns the first mismatch offset, or
+// lim.
+__device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const Pair Q, int64_t x0,
+                                           int64_t y0, int64_t lim0)
+{
+    const int tid = threadIdx.x;
+    const int64_t loc = min(lim0, (int64_t)max(0, P.local_chunks) * CHUNK_BYTES);
+    if (tid == 0 && loc > CHUNK_BYTES) {
+        bulk_prefetch_l2(Q.A, Q.n, x0 + CHUNK_BYTES, loc - CHUNK_BYTES);
+        bulk_prefetch_l2(Q.B, Q.m, y0 + CHUNK_BYTES, loc - CHUNK_BYTES);
+    }
+    int64_t off = 0;
+    for (; off < loc; off += CHUNK_BYTES) {
+        const int64_t r = chunk_scan(P, S, Q.A, Q.n, Q.B, Q.m, x0 + off, y0 + off, min((int64_t)CHUNK_BYTES, lim0 - off));
+        if (r >= 0)
+            return off + r;
+    }
+    while (off < lim0) {
+        const int64_t len = min(lim0 - off, (int64_t)JOB_MAX_CHUNKS * CHUNK_BYTES);
+        const int64_t r = run_job(P, S, Q, x0 + off, y0 + off, len);
+        if (r < len)
+            return off + r;
+        off += len;
+    }
+    return lim0;
 }
 
 // ------------------------------------------------------------------ group
@@ -531,13 +695,14 @@ __device__ bool group_sync(const LvArgs &P, GroupCtl *gc, int G, const Smem S)
 constexpr int OCAP = 1024;     // open slides listed per round (pipelined rounds)
 constexpr int DCAP = 3 * OCAP; // deferred diagonals: neighbours of open ones
 
-size_t lv_tiles_smem_bytes(int smax, int h)
+size_t lv_tiles_smem_bytes(int smax, int h, int stage)
 {
     (void)h;
     // two frontier buffers and the open-slide list, each smax + 2*HMAX + 2;
-    // two open lists of OCAP (diagonal, start row); DCAP deferred diagonals
+    // two open lists of OCAP (diagonal, start row); DCAP deferred diagonals;
+    // then, with a stage, one chunk's bulk-copy staging (128-byte aligned)
     return 256 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2) +
-           sizeof(int32_t) * (4 * (size_t)OCAP + DCAP);
+           sizeof(int32_t) * (4 * (size_t)OCAP + DCAP) + (stage ? 128 + stage_bytes<CHUNK_BYTES>() : 0);
 }
 
 // The frontier of round r (buffers alternate by parity).
@@ -558,6 +723,7 @@ __device__ Smem carve(const LvArgs &P)
     S.kf = S.nL + 6;
     S.nR = S.nL + 7;
     S.jd = reinterpret_cast<JobDesc *>(p + 192);
+    S.jring = reinterpret_cast<int *>(p + 48);
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -571,6 +737,8 @@ __device__ Smem carve(const LvArgs &P)
     S.Lc0 = S.Ld1 + OCAP;
     S.Lc1 = S.Lc0 + OCAP;
     S.D = S.Lc1 + OCAP;
+    p = reinterpret_cast<unsigned char *>(S.D + DCAP);
+    S.stg = P.stage ? reinterpret_cast<unsigned char *>(((uintptr_t)p + 127) & ~(uintptr_t)127) : nullptr;
     S.err = &P.ctl->error;
     S.diag = P.ctl->diag;
     return S;
@@ -712,7 +880,7 @@ __device__ __forceinline__ void cta_slides(const LvArgs &P, const Smem S, const 
         const int64_t lim = S.bcl[3];
         __syncthreads();
         const int64_t rr = long_slide(P, S, Q, c, c + d, lim - c);
-        if (lim - c > (int64_t)max(1, P.local_chunks) * CHUNK_BYTES) // published as a job
+        if (lim - c > (int64_t)max(0, P.local_chunks) * CHUNK_BYTES) // published as a job
             C.longs++;
         if (tid < 32)
             prefetch_next(Q.A, Q.n, Q.B, Q.m, c + rr, c + rr + d);
@@ -834,7 +1002,10 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
             RoundArgs RA = round_args(P, S, Q, tau, max(ra, blo), min(rb - 1, bhi), off, a, b);
             RA.tid = tid - 32 * sli;
             RA.nt = nt - 32 * nsl;
-            const RoundCount rc = tile_round<2048 / CTA_THREADS, true>(RA);
+            // one diagonal per thread when the range fits (narrow bands):
+            // the wide form's unrolled batch would be mostly idle slots
+            const RoundCount rc = RA.hi - RA.lo < RA.nt ? tile_round<1, true>(RA)
+                                                        : tile_round<2048 / CTA_THREADS, true>(RA);
             C.slide += rc.slide;
             C.mism += rc.mism;
         }
@@ -1240,7 +1411,9 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 return false;
             if (st == 3)
                 break;
-            help_one(P, S, 1);
+            const Wake wk{T.left >= 0 ? &P.ctl->flags[T.left] : nullptr,
+                          T.right >= 0 ? &P.ctl->flags[T.right] : nullptr, want};
+            help_one(P, S, 16, &wk);
         }
         int32_t *edge = frontier(S, t - 1);
         if (tid < h) {
@@ -1287,6 +1460,13 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
     if (threadIdx.x == 0) { // no job cached (read before the first group barrier)
         S.jd->jid = 0;
         S.jd->slot = -1;
+        *S.jring = 0;
+        if (S.stg) {
+            const Stage T = stage_of(S.stg);
+            mbar_init(T.bar, 1);
+            *T.phase = 0;
+            fence_mbar_init();
+        }
     }
     const uint64_t deadline = gtimer() + P.budget_ns;
     int cls = 0;
@@ -1335,7 +1515,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
 
 cudaError_t launch_lv_tiles(const LvArgs &P, int grid, cudaStream_t s)
 {
-    const size_t smem = lv_tiles_smem_bytes(P.smax, P.h);
+    const size_t smem = lv_tiles_smem_bytes(P.smax, P.h, P.stage);
     cudaError_t e =
         cudaFuncSetAttribute(lv_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
@@ -1394,8 +1574,11 @@ __global__ void lcp_query_kernel(const uint8_t *A, int64_t n, const uint8_t *B, 
 // Method 2: every CTA claims chunks of the queries' slots (published by the
 // host: claim = 1 << 32, result = lim) until each slot is exhausted; the
 // answers stay in the slots.
-__global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots)
+__device__ uint32_t g_lcp_grid_err; // status word of the test launches below
+
+__global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots, int stage)
 {
+    extern __shared__ __align__(128) unsigned char gsm[];
     __shared__ unsigned long long s_min;
     __shared__ long long s_bcl[4];
     __shared__ int s_bc[8];
@@ -1405,14 +1588,25 @@ __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, i
     S.bc = s_bc;
     S.bcl = s_bcl;
     S.jd = &s_jd;
+    S.err = &g_lcp_grid_err;
+    S.stg = stage ? gsm : nullptr;
+    LvArgs P{};
+    P.spin_ns = 2000000000ull;
     if (threadIdx.x == 0) {
         s_jd.jid = 0;
         s_jd.slot = -1;
+        if (stage) {
+            const Stage T = stage_of(gsm);
+            mbar_init(T.bar, 1);
+            *T.phase = 0;
+            fence_mbar_init();
+        }
     }
+    __syncthreads();
     for (int j = 0; j < nslots; j++) {
         const int s = (j + (int)blockIdx.x) % nslots;
         // claims until a chunk lies past the end or the best mismatch
-        claim_loop(S, &slots[s], s, 0ull, INT32_MAX);
+        claim_loop(P, S, &slots[s], s, 0ull, INT32_MAX);
     }
 }
 
@@ -1423,8 +1617,17 @@ cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, in
 {
     if (q == 0)
         return cudaSuccess;
-    if (method == 2) {
-        lcp_grid_kernel<<<grid, CTA_THREADS, 0, s>>>(slots, (int)q);
+    if (method == 2 || method == 7) {
+        // 2: register sweeps; 7: the same claims scanned through a bulk-copy stage
+        const int stage = method == 7;
+        const size_t smem = stage ? stage_bytes<CHUNK_BYTES>() : 0;
+        if (stage) {
+            const cudaError_t e =
+                cudaFuncSetAttribute(lcp_grid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess)
+                return e;
+        }
+        lcp_grid_kernel<<<grid, CTA_THREADS, smem, s>>>(slots, (int)q, stage);
         return cudaGetLastError();
     }
     HashArgs H{};

@@ -47,7 +47,7 @@ def _lcp_cases(rng):
     return A, B, np.array(xs), np.array(ys)
 
 
-@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("method", [0, 1, 2, 7])
 @pytest.mark.parametrize("offset", [0, 3, 13])
 def test_lcp_methods_match_oracle(ctx, orc, method, offset):
     from paper_2306_17461_gb300 import binding as ed
@@ -63,7 +63,9 @@ def test_lcp_methods_match_oracle(ctx, orc, method, offset):
 
 
 def test_lcp_grid_long_runs(ctx, orc):
-    """Runs of hundreds of KiB: the whole-grid slide (chunks, atomicMin)."""
+    """Runs of hundreds of KiB: the whole-grid slide (chunks, atomicMin),
+    with each chunk read by register sweeps (2) or staged in shared memory
+    by bulk copies (7), at every alignment of the pair of starts."""
     from paper_2306_17461_gb300 import binding as ed
 
     rng = np.random.default_rng(3)
@@ -75,10 +77,21 @@ def test_lcp_grid_long_runs(ctx, orc):
         B[p] ^= 0x5A
     xs = np.array([0, 1, 123_458, 500_000, 1_000_004, 1_000_005, 2_000_000, 2_999_991, 17])
     ys = xs.copy()
-    for method in (1, 2, 0):
+    for method in (1, 2, 7, 0):
         got = ed.ed_lcp_dev(ctx.h, dev(A), dev(B), xs, ys, method)
         want = np.array([orc.lcp(A, B, int(x), int(y)) for x, y in zip(xs, ys)])
         assert np.array_equal(got, want), method
+    # every (x mod 16, y mod 16) with a mismatch far inside, near a chunk end
+    # and at the very end of the strings
+    dA, dB = dev(A), dev(B)
+    for sx in range(16):
+        xs2 = np.array([sx + 16 * k for k in (0, 40_000, 62_500)])
+        for sy in range(0, 16, 5):
+            ys2 = xs2 - sx + sy
+            for method in (2, 7):
+                got = ed.ed_lcp_dev(ctx.h, dA, dB, xs2, ys2, method)
+                want = np.array([orc.lcp(A, B, int(x), int(y)) for x, y in zip(xs2, ys2)])
+                assert np.array_equal(got, want), (method, sx, sy)
 
 
 @pytest.mark.parametrize("length", [0, 1, 15, 16, 17, 255, 4095, 4096, 4097, 100_003, 1_000_000])
