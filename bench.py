@@ -159,6 +159,8 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+TUNE_TABLE = os.path.join(ROOT, "paper_2306_17461_gb300", "tune_table.tsv")
+
 # the translation unit of lv_tiles_kernel: the sources its counters depend on
 TILE_KERNEL_SOURCES = ("ed_device.cuh", "lv_kernels.cuh", "lv_round.cuh", "lv_tiles.cu")
 
@@ -262,15 +264,15 @@ def pair_record(pair, k, st, ms, peak):
 
 
 # ------------------------------------------------------------------ GPU arm
-def time_pairs(ed, ctx, dA, dB, stream, steps, warmup, flush=None):
-    """Runs every pair once per step through ed_distance_dev; returns the
-    CUDA-event time of each step (ms) and each pair's (k, stats, kernel ms)
-    of the timed steps."""
+def time_pairs(ed, ctxs, dA, dB, stream, steps, warmup, flush=None):
+    """Runs every pair once per step through ed_distance_dev (pair i on
+    context ctxs[i]); returns the CUDA-event time of each step (ms) and each
+    pair's (k, stats, kernel ms) of the timed steps."""
     import torch
 
     for _ in range(warmup):
         for i in range(len(dA)):
-            ed.ed_distance_dev(ctx.h, dA[i], dB[i], stream)
+            ed.ed_distance_dev(ctxs[i].h, dA[i], dB[i], stream)
     torch.cuda.synchronize()
     evs, recs = [], []
     for s in range(steps):
@@ -280,12 +282,24 @@ def time_pairs(ed, ctx, dA, dB, stream, steps, warmup, flush=None):
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(len(dA)):
-            k = ed.ed_distance_dev(ctx.h, dA[i], dB[i], stream)
-            recs.append((i, k, ed.ed_last_stats(ctx.h)))
+            k = ed.ed_distance_dev(ctxs[i].h, dA[i], dB[i], stream)
+            recs.append((i, k, ed.ed_last_stats(ctxs[i].h)))
         e1.record(stream)
         evs.append((e0, e1))
     torch.cuda.synchronize()
     return [e0.elapsed_time(e1) for e0, e1 in evs], recs
+
+
+def pair_contexts(ed, args, D, pairs, lcp_mode=None):
+    """One context per pair: with the tuning table, each pair's launch
+    parameters come from its row (the expected distance given as the
+    pair's planted edit count, as a caller that knows its data would)."""
+    tune = 1 if (args.tune and os.path.exists(TUNE_TABLE)) else 0
+    extra = {}
+    if lcp_mode is not None:
+        extra["lcp_mode"] = lcp_mode
+    return [ed.Context(device=D.local, block_rounds=args.block_rounds, hash_block=args.hash_block, tune=tune,
+                       distance_hint=int(p.edits) if tune else 0, **extra) for p in pairs], tune
 
 
 def summarize(pairs, tags, recs, peak):
@@ -306,9 +320,8 @@ def run_single(args, D: Dist):
     torch.cuda.set_device(D.local)
     dev = torch.device("cuda", D.local)
     pairs, desc, tags = make_workload(args.workload, args)
-    lcp_mode = {"direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH, "bhash": ed.ED_LCP_BHASH}[args.lcp]
-    ctx = ed.Context(device=D.local, lcp_mode=lcp_mode, block_rounds=args.block_rounds,
-                     hash_block=args.hash_block)
+    lcp_mode = {"auto": None, "direct": ed.ED_LCP_DIRECT, "hash": ed.ED_LCP_HASH, "bhash": ed.ED_LCP_BHASH}[args.lcp]
+    ctxs, tuned = pair_contexts(ed, args, D, pairs, lcp_mode)
     dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
     dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
     stream = torch.cuda.current_stream()
@@ -322,7 +335,7 @@ def run_single(args, D: Dist):
     D.barrier()
     clocks = Clocks(D.local)
     clocks.start()
-    step_ms, recs = time_pairs(ed, ctx, dA, dB, stream, args.steps, args.warmup, flush)
+    step_ms, recs = time_pairs(ed, ctxs, dA, dB, stream, args.steps, args.warmup, flush)
     D.barrier()
     clk = clocks.stop()
     ms = sum(step_ms)
@@ -336,18 +349,19 @@ def run_single(args, D: Dist):
     hA = [torch.from_numpy(p.A).pin_memory() for p in pairs]
     hB = [torch.from_numpy(p.B).pin_memory() for p in pairs]
     for i in range(len(pairs)):
-        ed.ed_distance(ctx.h, hA[i], hB[i])
+        ed.ed_distance(ctxs[i].h, hA[i], hB[i])
     torch.cuda.synchronize()
     D.barrier()
     t0 = time.perf_counter()
     e_ext = 0
     for _ in range(args.steps):
         for i in range(len(pairs)):
-            ed.ed_distance(ctx.h, hA[i], hB[i])
-            e_ext += ed.ed_last_stats(ctx.h)["extensions"]
+            ed.ed_distance(ctxs[i].h, hA[i], hB[i])
+            e_ext += ed.ed_last_stats(ctxs[i].h)["extensions"]
     e2e_s = D.max(time.perf_counter() - t0)
     h2d = sum(int(p.A.size + p.B.size) for p in pairs)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     secs = D.max(ms / 1e3)
     ext_all = D.sum(ext)
     achieved = (cbytes / (kms / 1e3)) / 1e9 if kms else 0.0
@@ -366,12 +380,13 @@ def run_single(args, D: Dist):
         "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": desc, "lcp": args.lcp, "pairs_per_step": len(pairs), "l2": l2_note,
-                   "parallelism": f"replicas x{D.ws}"},
+                   "parallelism": f"replicas x{D.ws}",
+                   "launch": "tuning table, distance hint = planted edits" if tuned else "built-in defaults"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                      "kernel": "lv_tiles_kernel",
                      "traffic": profile_traffic(f"lv_tiles_{args.workload}.md")
-                     if args.lcp == "direct" and args.ks == DEFAULT_KS and not args.n else None,
+                     if args.lcp in ("auto", "direct") and args.ks == DEFAULT_KS and not args.n else None,
                      "algorithmic_bytes_per_launch": cbytes / max(1, len(recs)),
                      "ns_per_round": head["ns_per_round"] if head else None,
                      "limiter": head["regime"] if head else "see per_pair"},
@@ -396,13 +411,14 @@ def run_single_extra(args, D: Dist, name: str, reps: int = 3):
     sub.n = 0
     sub.ks = DEFAULT_KS
     pairs, desc, tags = make_workload(name, sub)
-    ctx = ed.Context(device=D.local)
+    ctxs, _ = pair_contexts(ed, args, D, pairs)
     dA = [torch.from_numpy(p.A).to(dev) for p in pairs]
     dB = [torch.from_numpy(p.B).to(dev) for p in pairs]
     in_bytes = sum(int(p.A.size + p.B.size) for p in pairs)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if in_bytes < (256 << 20) else None
-    _, recs = time_pairs(ed, ctx, dA, dB, torch.cuda.current_stream(), reps, 1, flush)
-    ctx.close()
+    _, recs = time_pairs(ed, ctxs, dA, dB, torch.cuda.current_stream(), reps, 1, flush)
+    for c in ctxs:
+        c.close()
     peak, _ = peaks()
     out = summarize(pairs, tags, recs, peak)
     del dA, dB, flush
@@ -703,7 +719,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="large", choices=["mid", "small", "large", "batch", "serve", "lcplen"])
-    ap.add_argument("--lcp", default="direct", choices=["direct", "hash", "bhash"])
+    ap.add_argument("--lcp", default="auto", choices=["auto", "direct", "hash", "bhash"],
+                    help="auto: the tuning table's choice (direct without a table)")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="built-in launch parameters instead of the tuning table")
     ap.add_argument("--hash-block", type=int, default=0, help="block size b of --lcp bhash (0: 32)")
     ap.add_argument("--ks", default=DEFAULT_KS)
     ap.add_argument("--skews", default="0.5,0.9,0.99,0.999,0.9999")

@@ -74,6 +74,22 @@ typedef struct {
                                  string length (at most 2^28) */
     int hash_block;           /* block size b of ED_LCP_BHASH (1..4096);
                                  0 = 32 */
+    int warp_cap;             /* bytes one warp compares before a slide
+                                 goes to the whole CTA (>= 512); 0 = 4096 */
+    int local_chunks;         /* 16 KiB chunks a CTA compares alone before
+                                 its long slide is opened to other CTAs;
+                                 0 = 1, -1 = none */
+    int help_div;             /* while the band is narrow, 1/help_div of a
+                                 group's CTAs hold no tile and serve long
+                                 slides; 0 = 8, -1 = none */
+    int64_t distance_hint;    /* expected distance of single pairs (0 =
+                                 unknown); selects the tuning-table row */
+    int tune;                 /* 1: launch parameters of single-pair calls
+                                 that this configuration leaves at 0 come
+                                 from the tuning table; 0 = off */
+    const char *tune_table;   /* path of the tuning table; NULL = the
+                                 tune_table.tsv installed beside the
+                                 library.  Read by ed_create only. */
 } ed_config;
 
 typedef struct {
@@ -100,6 +116,19 @@ typedef struct {
 
 /* Fills *cfg with the defaults described in ed_config. */
 int ed_config_default(ed_config *cfg);
+
+/* The tuning-table row for a pair of lengths n, m with an expected
+ * distance (0 = unknown, taken as an edit rate of 1e-4): sets lcp_mode,
+ * block_rounds, tile_width, warp_cap, local_chunks and help_div of *cfg to
+ * the row's values (the other fields are left as they are).  The table is a
+ * text file (table = its path; NULL = tune_table.tsv beside the library)
+ * whose rows give, for max(n, m) in [n_lo, n_hi) and distance / max(n, m) in
+ * [rate_lo, rate_hi), the parameters a measured sweep found fastest:
+ * columns n_lo n_hi rate_lo rate_hi lcp_mode block_rounds tile_width
+ * warp_cap local_chunks help_div ('#' starts a comment); the first matching
+ * row is taken.  Host only.  ED_EINVAL when the table cannot be read or a
+ * row is malformed, ED_ENOTFOUND when no row matches. */
+int ed_tune_lookup(const char *table, size_t n, size_t m, int64_t distance_hint, ed_config *cfg);
 
 /* Creates a context on cfg->device (cfg may be NULL for defaults).  Sizes
  * its memory pool lazily inside the budget.  *out receives the context. */

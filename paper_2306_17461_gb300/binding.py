@@ -43,6 +43,12 @@ class ed_config(ctypes.Structure):
         ("block_rounds", ctypes.c_int),
         ("max_rounds", ctypes.c_int64),
         ("hash_block", ctypes.c_int),
+        ("warp_cap", ctypes.c_int),
+        ("local_chunks", ctypes.c_int),
+        ("help_div", ctypes.c_int),
+        ("distance_hint", ctypes.c_int64),
+        ("tune", ctypes.c_int),
+        ("tune_table", ctypes.c_char_p),
     ]
 
 
@@ -70,6 +76,7 @@ _lib = None
 _P, _S, _I, _U64, _I64 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_uint64, ctypes.c_int64
 _SIGS = {
     "ed_config_default": (_I, [_P]),
+    "ed_tune_lookup": (_I, [ctypes.c_char_p, _S, _S, _I64, _P]),
     "ed_create": (_I, [_P, _P]),
     "ed_destroy": (_I, [_P]),
     "ed_strerror": (ctypes.c_char_p, [_I]),
@@ -169,6 +176,15 @@ def _stream_ptr(stream):
 def ed_config_default() -> ed_config:
     c = ed_config()
     _check(None, load().ed_config_default(ctypes.byref(c)), "ed_config_default")
+    return c
+
+
+def ed_tune_lookup(n: int, m: int, distance_hint: int = 0, table: str | None = None) -> ed_config:
+    """The tuning-table row for lengths n, m (include/ed.h), as an ed_config
+    whose other fields are the defaults."""
+    c = ed_config_default()
+    _check(None, load().ed_tune_lookup(table.encode() if table else None, n, m, distance_hint, ctypes.byref(c)),
+           "ed_tune_lookup")
     return c
 
 
@@ -392,6 +408,8 @@ class Context:
     def __init__(self, **cfg):
         c = ed_config_default()
         for key, v in cfg.items():
+            if key == "tune_table" and isinstance(v, str):
+                v = v.encode()
             setattr(c, key, v)
         self.cfg = c
         self.h = ed_create(c)

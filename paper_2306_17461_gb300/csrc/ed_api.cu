@@ -13,6 +13,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <dlfcn.h>
+#include <fstream>
+#include <sstream>
 #include <map>
 #include <memory>
 #include <new>
@@ -152,10 +155,87 @@ struct TileOut {
     int64_t rt = 0, rr = 0;
 };
 
+// Launch parameters of one call, resolved from the context's
+// configuration, the tuning table and the built-in defaults.
+struct Eff {
+    int lcp_mode = ED_LCP_DIRECT; // AUTO resolved
+    int hash_block = 32;
+    int block_rounds = HMAX;
+    int tile_width = 64;
+    int warp_cap = 4096;
+    int local_chunks = 1;
+    int help_div = 8;
+};
+
+// One row of a tuning table: the launch parameters measured best for
+// max(n, m) in [n_lo, n_hi) and expected edit rate (distance / max(n, m))
+// in [r_lo, r_hi).
+struct TuneRow {
+    double n_lo, n_hi, r_lo, r_hi;
+    int lcp_mode, block_rounds, tile_width, warp_cap, local_chunks, help_div;
+};
+
+// Reads a tuning table (whitespace-separated columns n_lo n_hi r_lo r_hi
+// lcp block_rounds tile_width warp_cap local_chunks help_div; '#' starts a
+// comment).  Returns false if the file cannot be read or a row is malformed.
+bool read_tune_table(const char *path, std::vector<TuneRow> &rows)
+{
+    std::ifstream f(path);
+    if (!f)
+        return false;
+    rows.clear();
+    std::string line;
+    while (std::getline(f, line)) {
+        const size_t h = line.find('#');
+        if (h != std::string::npos)
+            line.resize(h);
+        std::istringstream ss(line);
+        TuneRow r{};
+        if (!(ss >> r.n_lo))
+            continue; // blank
+        if (!(ss >> r.n_hi >> r.r_lo >> r.r_hi >> r.lcp_mode >> r.block_rounds >> r.tile_width >> r.warp_cap >>
+              r.local_chunks >> r.help_div))
+            return false;
+        if (r.lcp_mode < ED_LCP_DIRECT || r.lcp_mode > ED_LCP_BHASH || r.block_rounds < 1 || r.block_rounds > HMAX ||
+            r.tile_width < 1 || r.tile_width > SMAX_LIMIT || r.warp_cap < 512 || r.local_chunks < 0 ||
+            r.help_div < 0)
+            return false;
+        rows.push_back(r);
+    }
+    return true;
+}
+
+// The table installed beside the library (tune_table.tsv in the directory
+// of libedgb300.so).
+std::string default_tune_path()
+{
+    Dl_info info{};
+    if (dladdr((void *)&read_tune_table, &info) && info.dli_fname) {
+        std::string p(info.dli_fname);
+        const size_t s = p.rfind('/');
+        return (s == std::string::npos ? std::string(".") : p.substr(0, s)) + "/tune_table.tsv";
+    }
+    return "tune_table.tsv";
+}
+
+// The row for a pair of lengths n, m with an expected distance hint (0:
+// unknown, taken as an edit rate of 1e-4), or null.
+const TuneRow *tune_lookup(const std::vector<TuneRow> &rows, int64_t n, int64_t m, int64_t hint)
+{
+    const double nm = (double)std::max<int64_t>(std::max(n, m), 1);
+    const double rate = hint > 0 ? (double)hint / nm : 1e-4;
+    for (const TuneRow &r : rows)
+        if (nm >= r.n_lo && nm < r.n_hi && rate >= r.r_lo && rate < r.r_hi)
+            return &r;
+    return nullptr;
+}
+
 } // namespace
 
 struct ed_ctx {
     ed_config cfg{};
+    Eff eff;                     // parameters of the call in progress
+    std::vector<TuneRow> tune;   // the tuning table (cfg.tune)
     int device = 0;
     int num_sms = 0;
     int grid = 0; // CTAs of the tile kernel
@@ -269,13 +349,46 @@ uint64_t count_extensions(int64_t n, int64_t m, int64_t k)
 
 bool bad_len(size_t n) { return n > (size_t)MAX_LEN; }
 
-bool hash_mode(const ed_ctx *ctx) { return ctx->cfg.lcp_mode == ED_LCP_HASH || ctx->cfg.lcp_mode == ED_LCP_BHASH; }
+bool hash_mode(const ed_ctx *ctx) { return ctx->eff.lcp_mode == ED_LCP_HASH || ctx->eff.lcp_mode == ED_LCP_BHASH; }
 
-// Stride of the context's prefix tables: 1 (full, Sec. 3.2) or the block
-// size of Sec. 3.3 (blocked, Alg. 2).
+// Stride of the call's prefix tables: 1 (full, Sec. 3.2) or the block size
+// of Sec. 3.3 (blocked, Alg. 2).
 int64_t hash_stride(const ed_ctx *ctx)
 {
-    return ctx->cfg.lcp_mode == ED_LCP_BHASH ? (int64_t)ctx->cfg.hash_block : 1;
+    return ctx->eff.lcp_mode == ED_LCP_BHASH ? (int64_t)ctx->eff.hash_block : 1;
+}
+
+// The call's launch parameters: built-in defaults, then (with cfg.tune and a
+// single pair of lengths n, m) the tuning table's row, then every field the
+// configuration sets explicitly.
+void resolve(ed_ctx *ctx, int64_t n, int64_t m, bool single)
+{
+    Eff e;
+    const ed_config &c = ctx->cfg;
+    e.hash_block = c.hash_block;
+    if (single && c.tune) {
+        if (const TuneRow *r = tune_lookup(ctx->tune, n, m, c.distance_hint)) {
+            e.lcp_mode = r->lcp_mode;
+            e.block_rounds = r->block_rounds;
+            e.tile_width = r->tile_width;
+            e.warp_cap = r->warp_cap;
+            e.local_chunks = r->local_chunks;
+            e.help_div = r->help_div;
+        }
+    }
+    if (c.lcp_mode != ED_LCP_AUTO)
+        e.lcp_mode = c.lcp_mode;
+    if (c.block_rounds > 0)
+        e.block_rounds = std::min(c.block_rounds, HMAX);
+    if (c.tile_width > 0)
+        e.tile_width = c.tile_width;
+    if (c.warp_cap > 0)
+        e.warp_cap = c.warp_cap;
+    if (c.local_chunks != 0)
+        e.local_chunks = std::max(0, c.local_chunks);
+    if (c.help_div != 0)
+        e.help_div = std::max(0, c.help_div);
+    ctx->eff = e;
 }
 
 // Waits for the prefix-hash scan last launched on s with the context's scan
@@ -329,8 +442,8 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
 {
     int r;
     const int np = (int)jobs.size();
-    const int h = ctx->cfg.block_rounds > 0 ? std::min(ctx->cfg.block_rounds, HMAX) : HMAX;
-    const int s0 = ctx->cfg.tile_width > 0 ? ctx->cfg.tile_width : 64;
+    const int h = ctx->eff.block_rounds;
+    const int s0 = ctx->eff.tile_width;
     // classes, ascending group size; pairs by class, then cost, largest first
     std::vector<int> sizes;
     for (const TileJob &j : jobs)
@@ -470,7 +583,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.smax = (int32_t)smax;
     P.h = h;
     P.s0 = s0;
-    P.t2_cap = 4096;
+    P.t2_cap = ctx->eff.warp_cap;
     P.use_hash = jobs[0].TA != nullptr;
     P.hash_b = (int32_t)hash_stride(ctx);
     std::memcpy(P.pow2, ctx->pow2, sizeof(P.pow2));
@@ -478,8 +591,8 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.idle_ns = ctx->cfg.spin_limit_ns * 60;
     P.budget_ns = budget_ns;
     P.sync_rounds = 16 * h;
-    P.help_div = 8;
-    P.local_chunks = 1;
+    P.help_div = ctx->eff.help_div;
+    P.local_chunks = ctx->eff.local_chunks;
     // bulk-copy staging of long-slide chunks when the tiles leave room for it
     P.stage = lv_tiles_smem_bytes((int)smax, h, 1) <= (size_t)ctx->smem_optin ? 1 : 0;
     CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
@@ -649,6 +762,26 @@ const char *ed_strerror(int s)
     }
 }
 
+int ed_tune_lookup(const char *table, size_t n, size_t m, int64_t distance_hint, ed_config *cfg)
+{
+    if (!cfg || distance_hint < 0)
+        return ED_EINVAL;
+    std::vector<TuneRow> rows;
+    const std::string path = table ? std::string(table) : default_tune_path();
+    if (!read_tune_table(path.c_str(), rows))
+        return ED_EINVAL;
+    const TuneRow *r = tune_lookup(rows, (int64_t)n, (int64_t)m, distance_hint);
+    if (!r)
+        return ED_ENOTFOUND;
+    cfg->lcp_mode = r->lcp_mode;
+    cfg->block_rounds = r->block_rounds;
+    cfg->tile_width = r->tile_width;
+    cfg->warp_cap = r->warp_cap;
+    cfg->local_chunks = r->local_chunks > 0 ? r->local_chunks : -1;
+    cfg->help_div = r->help_div > 0 ? r->help_div : -1;
+    return ED_OK;
+}
+
 int ed_config_default(ed_config *cfg)
 {
     if (!cfg)
@@ -681,8 +814,16 @@ int ed_create(ed_ctx **out, const ed_config *cfg)
     if (c->cfg.hash_block == 0)
         c->cfg.hash_block = 32;
     if (c->cfg.lcp_mode < 0 || c->cfg.lcp_mode > 3 || c->cfg.tile_width < 0 || c->cfg.block_rounds < 0 ||
-        c->cfg.tile_width > SMAX_LIMIT || c->cfg.hash_block < 1 || c->cfg.hash_block > 4096)
+        c->cfg.tile_width > SMAX_LIMIT || c->cfg.hash_block < 1 || c->cfg.hash_block > 4096 ||
+        c->cfg.warp_cap < 0 || (c->cfg.warp_cap > 0 && c->cfg.warp_cap < 512) || c->cfg.local_chunks < -1 ||
+        c->cfg.help_div < -1 || c->cfg.distance_hint < 0)
         return ED_EINVAL;
+    if (c->cfg.tune) {
+        const std::string path = c->cfg.tune_table ? std::string(c->cfg.tune_table) : default_tune_path();
+        if (!read_tune_table(path.c_str(), c->tune))
+            return ED_EINVAL;
+        c->cfg.tune_table = nullptr; // the caller's string is not kept
+    }
     int dev = c->cfg.device;
     if (dev < 0)
         CK(cudaGetDevice(&dev));
@@ -760,6 +901,7 @@ int ed_distance_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, s
     std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     ctx->last = ed_stats{};
+    resolve(ctx, (int64_t)n, (int64_t)m, true);
     return run_pair(ctx, A, (int64_t)n, B, (int64_t)m, (cudaStream_t)stream, nullptr, 0, k);
 }
 
@@ -770,6 +912,7 @@ int ed_distance(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_
     std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     ctx->last = ed_stats{};
+    resolve(ctx, (int64_t)n, (int64_t)m, true);
     int r;
     if ((r = ensure(ctx, ctx->strA, n + 64)) != ED_OK || (r = ensure(ctx, ctx->strB, m + 64)) != ED_OK)
         return r;
@@ -792,6 +935,7 @@ static int frontiers_to_host(ed_ctx *ctx, const uint8_t *A, size_t n, const uint
     std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     ctx->last = ed_stats{};
+    resolve(ctx, (int64_t)n, (int64_t)m, true);
     const size_t cnt = (size_t)(t_max + 1) * (size_t)(2 * t_max + 1);
     int r;
     if ((r = ensure(ctx, ctx->dump, cnt * sizeof(int32_t))) != ED_OK)
@@ -1187,6 +1331,7 @@ int ed_distance_batch_dev(ed_ctx *ctx, size_t np, const uint8_t *const *A, const
     std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     ctx->last = ed_stats{};
+    resolve(ctx, 0, 0, false);
     if (np == 0)
         return ED_OK;
     return batch_core(ctx, np, A, n, B, m, k_out, (cudaStream_t)stream);
@@ -1206,6 +1351,7 @@ int ed_distance_batch(ed_ctx *ctx, size_t np, const uint8_t *const *A, const siz
     std::lock_guard<std::mutex> g(ctx->api_mu);
     CK(cudaSetDevice(ctx->device));
     ctx->last = ed_stats{};
+    resolve(ctx, 0, 0, false);
     if (np == 0)
         return ED_OK;
     int r;
@@ -1289,6 +1435,7 @@ static void engine_loop(ed_ctx *ctx)
             }
         }
         std::unique_lock<std::mutex> api(ctx->api_mu);
+        resolve(ctx, 0, 0, false);
         const size_t L = ctx->live.size();
         std::vector<int64_t> result(L, 0);
         std::vector<char> done(L, 0);

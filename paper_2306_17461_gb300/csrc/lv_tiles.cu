@@ -386,11 +386,11 @@ struct Wake {
 // (checked along with each claim).  Returns the number of claims made and
 // answered.
 __device__ int claim_loop(const LvArgs &P, const Smem S, JobSlot *sl, int s, unsigned long long w0, int budget,
-                          const Wake *wake = nullptr)
+                          const Wake *wake = nullptr, unsigned long long best0 = ~0ull)
 {
     const int tid = threadIdx.x;
     unsigned long long w = 0;     // thread 0: the current claim word
-    unsigned long long best = ~0ull; // thread 0: the result read with it (~0: none)
+    unsigned long long best = best0; // thread 0: the result read with it (~0: none)
     if (tid == 0)
         w = w0 ? w0 : atomicAdd(&sl->claim, 1ull);
     int made = 0;
@@ -519,10 +519,13 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
             }
         }
     }
-    __syncthreads();
-    for (uint32_t w = tid; w * 64 < nch; w += blockDim.x)
-        sl->bits[w] = 0ull;
-    __threadfence();
+    // warp 0 clears the marks the job will use (each lane fenced before the
+    // barrier, so that the release below orders them before the job opens)
+    if (tid < 32) {
+        for (uint32_t w = tid; w * 64 < nch; w += 32)
+            sl->bits[w] = 0ull;
+        __threadfence();
+    }
     __syncthreads();
     // ------------------------------------------------ publish
     if (tid == 0) {
@@ -560,7 +563,7 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     __syncthreads();
     const unsigned long long w0 = (unsigned long long)S.bcl[2];
     __syncthreads();
-    claim_loop(P, S, sl, sidx, w0, 1); // chunk 0
+    claim_loop(P, S, sl, sidx, w0, 1, nullptr, (unsigned long long)lim); // chunk 0 (no mismatch known yet)
     // ------------------------------------------------ watch
     // warp 0 looks at the marks (acquire), then at the result and the claim
     // count: final once every chunk up to the one holding the best mismatch
@@ -1076,6 +1079,119 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
     return BlockOut{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens, C.tm[0], C.tm[1], kfound >= 0 ? 1 : 0};
 }
 
+// The open slides of a lean round (out of line: most rounds have none):
+// one warp each, up to t2_cap bytes, then the whole CTA for those still
+// open.  Every thread calls it; the final rows are visible to every thread
+// when it returns.
+__device__ __forceinline__ void lean_slides(const LvArgs &P, const Smem S, const Pair Q, int32_t *cur, int64_t off,
+                                         int32_t *Ld, const int32_t *Lc, int nlo, int64_t a, int64_t b, int pr,
+                                         Counters &C)
+{
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    warp_slides(P, Q, cur, off, Ld, Lc, nlo, a, b, warp, nw, C, S.left + pr);
+    __syncthreads();
+    if (S.left[pr])
+        cta_slides(P, S, Q, cur, off, Ld, Lc, nlo, a, b, C);
+    if (threadIdx.x == 0)
+        S.left[pr] = 0;
+    __syncthreads();
+}
+
+// Rounds t .. t+h-1 on a narrow tile (the trapezoid, tile and halos, fits
+// one diagonal per thread): every thread computes its diagonal of the round
+// (start row from the three predecessors, then the word slide); after one
+// barrier the slides the words left open, if any, go to one warp each (up to
+// t2_cap bytes) and then to the whole CTA; every thread then reads the
+// termination test of the round itself from the final row of d = m - n.
+// One barrier a round when no slide is left open, three when one is.
+__device__ __forceinline__ BlockOut run_block_lean(const LvArgs &P, const Smem S, const Pair Q, int32_t *dump,
+                                                int32_t dump_tmax, unsigned long long *res, GroupCtl *gc, int64_t t,
+                                                int h, int64_t a, int64_t b)
+{
+    const int tid = threadIdx.x;
+    const int64_t n = Q.n, m = Q.m, target = m - n;
+    const int32_t n32 = (int32_t)n, m32 = (int32_t)m, mn = (int32_t)(m - n);
+    const int64_t off = a - h - 1; // smem index = d - off
+    Counters C;
+    int64_t kfound = -1;
+    if (tid == 0) {
+        S.nL[0] = S.nL[1] = 0;
+        S.left[0] = S.left[1] = 0;
+    }
+    __syncthreads();
+    int r = 0;
+    for (; r < h && kfound < 0; r++) {
+        const uint64_t tr0 = clock64();
+        const int64_t tau = t + r;
+        const int pr = (int)(tau & 1);
+        const int32_t ra = (int32_t)(a - h + 1 + r), rb = (int32_t)(b + h - 1 - r); // computed range [ra, rb)
+        const int32_t blo = (int32_t)max(-tau, -n), bhi = (int32_t)min(tau, m);
+        int32_t *cur = frontier(S, tau);
+        const int32_t *prev = frontier(S, tau - 1);
+        int32_t *Ld = pr ? S.Ld1 : S.Ld0;
+        int32_t *Lc = pr ? S.Lc1 : S.Lc0;
+        int *nl = S.nL + pr;
+        const int32_t d = ra + tid;
+        if (d < rb) {
+            if (d < blo || d > bhi) {
+                cur[d - off] = NEG;
+            } else {
+                int32_t cc = 0;
+                if (tau > 0) {
+                    const int32_t x1 = prev[d - 1 - off], x2 = prev[d - off], x3 = prev[d + 1 - off];
+                    cc = min(max(x1, max(x2, x3) + 1), d <= mn ? n32 : m32 - d);
+                }
+                if (cc < 0 || cc + d < 0) {
+                    record_bad_row(S.err, S.diag, tau, prev, (int32_t)off, d, cc);
+                    cur[d - off] = NEG;
+                } else {
+                    const int32_t full = min(n32 - cc, m32 - cc - d);
+                    int32_t l = 0;
+                    if (full > 0) {
+                        uint2 wa, wb;
+                        uint32_t sh;
+                        words_load(Q.A, Q.B, n32, m32, cc, d, wa, wb, sh);
+                        l = words_lcp(wa, wb, sh, full);
+                    }
+                    if (l >= 0) {
+                        cur[d - off] = cc + l;
+                        if (d >= a && d < b) {
+                            C.slide += (uint32_t)l;
+                            C.mism += (l < full);
+                        }
+                    } else {
+                        const int j = atomicAdd(nl, 1); // at most one per thread: the list cannot fill
+                        Ld[j] = d;
+                        Lc[j] = cc;
+                        cur[d - off] = PENDING;
+                    }
+                }
+            }
+        }
+        if (tid == 0)
+            S.nL[pr ^ 1] = 0; // the other parity's list is free again
+        __syncthreads();
+        const int nlo = *nl;
+        if (nlo > 0)
+            lean_slides(P, S, Q, cur, off, Ld, Lc, nlo, a, b, pr, C);
+        // the round is final: every thread reads the termination test
+        if (target >= a && target < b && target >= blo && target <= bhi && cur[target - off] == n32)
+            kfound = tau;
+        if (dump && tau <= dump_tmax) {
+            const int64_t TT = dump_tmax;
+            for (int64_t e = max(a, -TT) + tid; e < min(b, TT + 1); e += blockDim.x)
+                dump[tau * (2 * TT + 1) + e + TT] = cur[e - off];
+        }
+        C.tm[0] += clock64() - tr0;
+    }
+    if (kfound >= 0 && tid == 0) {
+        atomicMin(&gc->done_k, (unsigned long long)kfound);
+        res[R_K] = (unsigned long long)kfound;
+    }
+    __syncthreads();
+    return BlockOut{C.slide, C.mism, C.hashq, C.coll, C.longs, C.opens, C.tm[0], C.tm[1], kfound >= 0 ? 1 : 0};
+}
+
 // Whether a CTA that is about to compute round t leaves the pair.  Once k
 // is known every CTA leaves at once, except with a frontier dump: a CTA may
 // lag its neighbours by a few blocks, so it first computes every round up
@@ -1343,7 +1459,10 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             t = t2;
         } else {
             // ------------------------------------------ h rounds
-            const BlockOut bo = run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
+            // a trapezoid of at most one diagonal per thread: the lean rounds
+            const BlockOut bo = (b - a) + 2 * h - 2 <= (int64_t)blockDim.x
+                                    ? run_block_lean(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b)
+                                    : run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
             C.slide += bo.slide;
             C.mism += bo.mism;
             C.hashq += bo.hashq;

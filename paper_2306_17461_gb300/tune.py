@@ -1,0 +1,183 @@
+"""Offline sweep of the single-pair kernel's launch parameters; writes the
+tuning table the library reads (ed_config.tune, include/ed.h).
+
+For each workload class -- the longer string's length n and the edit rate
+k / n, on seeded synthetic pairs shaped like the paper's workloads (Sec. 6:
+random strings with k planted insertions, deletions and substitutions) --
+the sweep starts from the built-in defaults and, one parameter at a time,
+keeps the value with the lowest median device time (coordinate descent):
+
+    block_rounds  rounds between neighbour exchanges
+    tile_width    diagonals per CTA in the first epoch
+    warp_cap      bytes one warp compares before the whole CTA takes a slide
+    local_chunks  16 KiB chunks a CTA compares alone before opening a slide
+    help_div      1/help_div of the CTAs serve long slides while the band is narrow
+    lcp_mode      direct comparison, or the prefix-hash search of Sec. 3.2 /
+                  Alg. 2 (blocked tables), every hash answer confirmed
+
+Every measured distance is checked against the first one of its pair (the
+parameters change the schedule, never the result).  Writes two files next to
+this module: tune_sweep.tsv (every measurement) and tune_table.tsv (one row
+per class, the format ed_tune_lookup reads; classes without a measurement
+take the nearest measured rate of their length).
+
+    python -m paper_2306_17461_gb300.tune [--reps 3] [--quick]
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import statistics
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+# class edges: length buckets and edit-rate buckets of the table
+N_EDGES = [0, 3e6, 3e7, 3e8, 1e12]
+R_EDGES = [0, 3e-6, 3e-5, 3e-4, 1.0]
+DEFAULTS = {"lcp_mode": 1, "block_rounds": 16, "tile_width": 64, "warp_cap": 4096, "local_chunks": 1,
+            "help_div": 8}
+CANDIDATES = {
+    "block_rounds": [4, 8, 16],
+    "tile_width": [16, 64, 256],
+    "warp_cap": [2048, 4096, 16384],
+    "local_chunks": [-1, 1, 4],
+    "help_div": [-1, 8, 4],
+    "lcp_mode": [1, 2, 3],
+}
+
+
+def workloads(quick: bool):
+    """(name, n, k, pair factory) per measured class: sigma = 4 uniform with
+    uniform planted edits at n = 1e6, 1e7, 1e8 and rates 1e-6 .. 1e-3, and the
+    n = 1e9 Zipf(1.1) pair with bursty edits."""
+    from paper_2306_17461_gb300 import workloads as W
+
+    out = []
+    ns = [10**6, 10**7] if quick else [10**6, 10**7, 10**8]
+    for n in ns:
+        for rate in (1e-6, 1e-5, 1e-4, 1e-3):
+            k = max(1, int(round(n * rate)))
+            out.append((f"uniform4 n={n} k={k}", n, k, lambda n=n, k=k: W.make_pair(7, n, k, sigma=4, extra=k)))
+    if not quick:
+        out.append(("zipf256-bursts n=1e9 k=1e4", 10**9, 10**4, lambda: W.single_large()))
+    return out
+
+
+def measure(ed, dA, dB, params, reps):
+    """Median device time (kernel + hash build) of one distance, and k."""
+    cfg = {"device": 0}
+    for key in ("block_rounds", "tile_width", "warp_cap", "local_chunks", "help_div", "lcp_mode"):
+        cfg[key] = params[key]
+    ctx = ed.Context(**cfg)
+    try:
+        ed.ed_distance_dev(ctx.h, dA, dB)  # warm-up
+        ms, k = [], None
+        for _ in range(reps):
+            k = ed.ed_distance_dev(ctx.h, dA, dB)
+            st = ed.ed_last_stats(ctx.h)
+            ms.append(st["kernel_ms"] + st["build_ms"])
+        return statistics.median(ms), k
+    finally:
+        ctx.close()
+
+
+def sweep(reps: int, quick: bool, log=print):
+    import torch
+
+    from paper_2306_17461_gb300 import binding as ed
+
+    rows = []
+    best_by_class = {}
+    for name, n, k_planted, make in workloads(quick):
+        p = make()
+        dA = torch.from_numpy(p.A).cuda()
+        dB = torch.from_numpy(p.B).cuda()
+        cur = dict(DEFAULTS)
+        t_def, k_ref = measure(ed, dA, dB, cur, reps)
+        rows.append((name, n, k_ref, dict(cur), t_def))
+        t_best = t_def
+        for key, values in CANDIDATES.items():
+            for v in values:
+                if v == cur[key]:
+                    continue
+                # the hash searches cost seconds at k = 1e5: measured below that
+                if key == "lcp_mode" and k_planted > 20_000:
+                    continue
+                trial = dict(cur, **{key: v})
+                t, k = measure(ed, dA, dB, trial, reps)
+                if k != k_ref:
+                    raise RuntimeError(f"{name}: distance {k} with {trial}, {k_ref} with the defaults")
+                rows.append((name, n, k, trial, t))
+                if t < t_best:
+                    t_best, cur = t, trial
+        log(f"{name}: k={k_ref} default {t_def:.3f} ms, best {t_best:.3f} ms with {cur}")
+        best_by_class[(n, k_ref / n)] = (cur, t_def, t_best)
+        del dA, dB
+        torch.cuda.empty_cache()
+    return rows, best_by_class
+
+
+def bucket(edges, v):
+    for i in range(len(edges) - 1):
+        if edges[i] <= v < edges[i + 1]:
+            return i
+    return len(edges) - 2
+
+
+def table_rows(best_by_class):
+    """One row per (length bucket, rate bucket): the measured class in it, or
+    the measured class of the same length bucket with the nearest rate."""
+    measured = {}
+    for (n, rate), (params, _, _) in best_by_class.items():
+        measured[(bucket(N_EDGES, n), bucket(R_EDGES, rate))] = (rate, params)
+    out = []
+    for i in range(len(N_EDGES) - 1):
+        have = [(b, v) for (a, b), v in measured.items() if a == i]
+        if not have:
+            continue
+        for j in range(len(R_EDGES) - 1):
+            mid = math.sqrt(max(R_EDGES[j], 1e-7) * R_EDGES[j + 1])
+            b, (rate, params) = min(have, key=lambda bv: abs(math.log(max(bv[1][0], 1e-9) / mid)))
+            out.append((N_EDGES[i], N_EDGES[i + 1], R_EDGES[j], R_EDGES[j + 1], params))
+    return out
+
+
+def write(rows, best_by_class, stamp):
+    keys = ["lcp_mode", "block_rounds", "tile_width", "warp_cap", "local_chunks", "help_div"]
+    with open(os.path.join(HERE, "tune_sweep.tsv"), "w") as f:
+        f.write(f"# single-pair kernel, median device ms of one distance ({stamp})\n")
+        f.write("# workload\tn\tk\t" + "\t".join(keys) + "\tms\n")
+        for name, n, k, params, t in rows:
+            f.write(f"{name}\t{n}\t{k}\t" + "\t".join(str(params[x]) for x in keys) + f"\t{t:.4f}\n")
+    with open(os.path.join(HERE, "tune_table.tsv"), "w") as f:
+        f.write(f"# tuning table of the single-pair kernel, from tune_sweep.tsv ({stamp})\n")
+        f.write("# rows: max(n, m) in [n_lo, n_hi), distance / max(n, m) in [rate_lo, rate_hi)\n")
+        f.write("# n_lo n_hi rate_lo rate_hi lcp_mode block_rounds tile_width warp_cap local_chunks help_div\n")
+        for n_lo, n_hi, r_lo, r_hi, p in table_rows(best_by_class):
+            f.write(f"{n_lo:g} {n_hi:g} {r_lo:g} {r_hi:g} " + " ".join(str(max(0, p[x]) if x in ("local_chunks", "help_div") else p[x]) for x in keys) + "\n")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--quick", action="store_true", help="n <= 1e7 only")
+    a = ap.parse_args()
+    import sys
+
+    sys.path.insert(0, os.path.dirname(HERE))
+    import torch
+
+    from paper_2306_17461_gb300 import binding
+
+    binding.load()
+    dev = torch.cuda.get_device_name(0)
+    rows, best = sweep(a.reps, a.quick)
+    write(rows, best, f"{dev}, {time.strftime('%Y-%m-%d')}")
+
+
+if __name__ == "__main__":
+    main()
