@@ -78,7 +78,7 @@ typedef struct {
                                  goes to the whole CTA (>= 512); 0 = 4096 */
     int local_chunks;         /* 16 KiB chunks a CTA compares alone before
                                  its long slide is opened to other CTAs;
-                                 0 = 1, -1 = none */
+                                 0 = none (open at once) */
     int help_div;             /* while the band is narrow, 1/help_div of a
                                  group's CTAs hold no tile and serve long
                                  slides; 0 = 8, -1 = none */

@@ -163,7 +163,7 @@ struct Eff {
     int block_rounds = HMAX;
     int tile_width = 64;
     int warp_cap = 4096;
-    int local_chunks = 1;
+    int local_chunks = 0;
     int help_div = 8;
 };
 
@@ -593,8 +593,12 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.sync_rounds = 16 * h;
     P.help_div = ctx->eff.help_div;
     P.local_chunks = ctx->eff.local_chunks;
-    // bulk-copy staging of long-slide chunks when the tiles leave room for it
-    P.stage = lv_tiles_smem_bytes((int)smax, h, 1) <= (size_t)ctx->smem_optin ? 1 : 0;
+    // bulk-copy staging of long-slide chunks (two stages: the owner streams
+    // its first chunks with the next one's copies in flight) when the tiles
+    // leave room for it
+    P.stage = lv_tiles_smem_bytes((int)smax, h, 2) <= (size_t)ctx->smem_optin
+                  ? 2
+                  : (lv_tiles_smem_bytes((int)smax, h, 1) <= (size_t)ctx->smem_optin ? 1 : 0);
     CK(cudaMemcpyAsync(ctx->pdesc.p, pd.data(), sizeof(PairDesc) * np, cudaMemcpyHostToDevice, s));
     CK(cudaMemsetAsync(ctx->ctl.p, 0, sizeof(LaunchCtl), s));
     CK(cudaMemsetAsync(ctx->gctl.p, 0, sizeof(GroupCtl) * ngroups, s));

@@ -583,47 +583,55 @@ constexpr size_t stage_bytes()
     return (size_t)CH + 16 + (size_t)CH + 32 + 16 + 16;
 }
 
-// The calling CTA compares A[x0 .. x0+len) with B[y0 .. y0+len) for
-// len <= CH (the chunk size) and returns the first mismatching offset, or
-// -1 if all are equal; needs x0 + len <= n and y0 + len <= m.  Thread 0
-// copies both windows into the stage by two bulk copies (aligned 16-byte
-// blocks, clipped to the blocks that overlap each string); every thread
-// waits on the stage's mbarrier, bounded by spin_ns (on expiry: *err set,
-// then one more bounded wait for the copies, and -2 returned), then
-// compares its 16-byte blocks of A with the B bytes paired with them (two
-// aligned 16-byte reads and a byte shift).  Bytes copied from outside a
-// string, or not copied at all, pair only with offsets outside [0, len).
-// Every thread must call it; s_min is a shared 64-bit scratch word.
-template <int CH>
-__device__ __noinline__ int64_t stage_scan(const Stage T, const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
-                                           int64_t x0, int64_t y0, int64_t len, unsigned long long *s_min,
-                                           uint64_t spin_ns, uint32_t *err)
+// A staged chunk: A[x0 .. x0+len) against B[y0 .. y0+len), len <= CH, with
+// x0 + len <= n and y0 + len <= m.  The A side is held in aligned 16-byte
+// blocks, block j starting sa bytes before A[x0] (offsets 16j - sa ..
+// 16j - sa + 15); the B bytes paired with block j are bytes qb .. qb + 15 of
+// the stage's B blocks j and j + 1.
+struct StagedChunk {
+    uint32_t sa, qb;
+    int64_t nblk, len;
+};
+
+// Thread 0: copies the chunk's aligned blocks into stage T by two bulk
+// copies completing on T's mbarrier (clipped to the blocks that overlap
+// each string: such a block lies in the same page as a valid byte).  Bytes
+// copied from outside a string, or not copied at all, pair only with
+// offsets outside [0, len).
+__device__ __forceinline__ StagedChunk stage_issue(const Stage T, const uint8_t *A, int64_t n, const uint8_t *B,
+                                                   int64_t m, int64_t x0, int64_t y0, int64_t len, bool issue)
 {
-    const int tid = threadIdx.x;
+    StagedChunk K;
     const uintptr_t pa = (uintptr_t)(A + x0);
-    const uint32_t sa = (uint32_t)(pa & 15);
-    const uintptr_t a0 = pa - sa;
-    const uintptr_t pbs = (uintptr_t)(B + y0) - sa; // B address paired with a0
-    const uint32_t qb = (uint32_t)(pbs & 15);
-    const uintptr_t b0 = pbs - qb;
-    const int64_t nblk = (sa + len + 15) >> 4; // A blocks holding offsets [0, len)
-    const uint32_t parity = *T.phase;
-    if (tid == 0) {
-        *s_min = ~0ull;
-        // A: blocks a0 .. a0 + 16*nblk, clipped to the last block of A
+    K.sa = (uint32_t)(pa & 15);
+    const uintptr_t a0 = pa - K.sa;
+    const uintptr_t pbs = (uintptr_t)(B + y0) - K.sa; // B address paired with a0
+    K.qb = (uint32_t)(pbs & 15);
+    const uintptr_t b0 = pbs - K.qb;
+    K.nblk = (K.sa + len + 15) >> 4; // A blocks holding offsets [0, len)
+    K.len = len;
+    if (issue) {
         const uintptr_t aend = (((uintptr_t)A + (uintptr_t)n - 1) & ~(uintptr_t)15) + 16;
-        const uint32_t la = (uint32_t)(min(a0 + 16 * (uintptr_t)nblk, aend) - a0);
-        // B: blocks b0 .. b0 + 16*(nblk+1), clipped to the blocks of B
+        const uint32_t la = (uint32_t)(min(a0 + 16 * (uintptr_t)K.nblk, aend) - a0);
         const uintptr_t bfirst = (uintptr_t)B & ~(uintptr_t)15;
         const uintptr_t bend = (((uintptr_t)B + (uintptr_t)m - 1) & ~(uintptr_t)15) + 16;
         const uintptr_t bs = max(b0, bfirst);
-        const uintptr_t be = min(b0 + 16 * (uintptr_t)(nblk + 1), bend);
+        const uintptr_t be = min(b0 + 16 * (uintptr_t)(K.nblk + 1), bend);
         const uint32_t lb = (uint32_t)(be - bs);
         mbar_arrive_tx(T.bar, la + lb);
         bulk_g2s(T.a, (const void *)a0, la, T.bar);
         bulk_g2s(T.b + (bs - b0), (const void *)bs, lb, T.bar);
     }
-    // wait for both copies (bounded)
+    return K;
+}
+
+// Every thread: waits for stage T's copies (phase *T.phase), bounded by
+// spin_ns.  On expiry *err is set, thread 0 gives the copies one more
+// bounded wait, the phase is passed and false is returned (to every
+// thread).
+__device__ __forceinline__ bool stage_wait(const Stage T, uint64_t spin_ns, uint32_t *err)
+{
+    const uint32_t parity = *T.phase;
     bool ok = mbar_test(T.bar, parity);
     if (!ok) {
         const uint64_t t0 = gtimer();
@@ -632,28 +640,37 @@ __device__ __noinline__ int64_t stage_scan(const Stage T, const uint8_t *A, int6
                 break;
         }
     }
-    if (!__syncthreads_and(ok)) {
-        // record, then give the copies one more bounded wait before the
-        // stage may be touched again
-        if (tid == 0) {
-            atomicCAS(err, 0u, 4u);
-            const uint64_t t1 = gtimer();
-            while (!mbar_test(T.bar, parity) && gtimer() - t1 < spin_ns) {
-            }
-            *T.phase = parity ^ 1u;
+    if (__syncthreads_and(ok))
+        return true;
+    if (threadIdx.x == 0) {
+        atomicCAS(err, 0u, 4u);
+        const uint64_t t1 = gtimer();
+        while (!mbar_test(T.bar, parity) && gtimer() - t1 < spin_ns) {
         }
-        __syncthreads();
-        return -2;
+        *T.phase = parity ^ 1u;
     }
+    __syncthreads();
+    return false;
+}
+
+// Every thread, after stage_wait: the first mismatching offset of the
+// staged chunk, or -1.  Each thread compares its 16-byte blocks of A with
+// the B bytes paired with them (two aligned 16-byte reads and a byte shift).
+// The stage is released (phase passed, reads ordered before later bulk
+// copies into it) before the result is combined.  s_min: a shared 64-bit
+// scratch word.
+__device__ __forceinline__ int64_t stage_compare(const Stage T, const StagedChunk K, unsigned long long *s_min)
+{
+    const int tid = threadIdx.x;
     int64_t best = -1;
-    for (int64_t j = tid; j < nblk && best < 0; j += blockDim.x) {
+    for (int64_t j = tid; j < K.nblk && best < 0; j += blockDim.x) {
         const uint4 va = *reinterpret_cast<const uint4 *>(T.a + 16 * j);
         const uint4 lo = *reinterpret_cast<const uint4 *>(T.b + 16 * j);
         const uint4 hi = *reinterpret_cast<const uint4 *>(T.b + 16 * j + 16);
-        const uint4 bs = shift_bytes(lo, hi, qb);
-        const int64_t o0 = 16 * j - (int64_t)sa;
+        const uint4 bs = shift_bytes(lo, hi, K.qb);
+        const int64_t o0 = 16 * j - (int64_t)K.sa;
         const int lo_i = o0 < 0 ? (int)-o0 : 0;
-        const int64_t hi64 = len - o0;
+        const int64_t hi64 = K.len - o0;
         const int hi_i = hi64 >= 16 ? 16 : (hi64 <= 0 ? 0 : (int)hi64);
         if (lo_i < hi_i) {
             uint64_t d0 = ((uint64_t)(va.y ^ bs.y) << 32) | (uint64_t)(va.x ^ bs.x);
@@ -670,21 +687,80 @@ __device__ __noinline__ int64_t stage_scan(const Stage T, const uint8_t *A, int6
                 best = o0 + 8 + ((__ffsll((long long)d1) - 1) >> 3);
         }
     }
-    // the stage is read: the next copies may overwrite it after this barrier
     fence_proxy_async_smem();
+    if (tid == 0)
+        *s_min = ~0ull;
     const int any = __syncthreads_or(best >= 0);
     if (tid == 0)
-        *T.phase = parity ^ 1u;
+        *T.phase ^= 1u;
     if (any) {
         if (best >= 0)
             atomicMin(s_min, (unsigned long long)best);
         __syncthreads();
         const int64_t r = (int64_t)*s_min;
-        __syncthreads(); // read by all before the next call resets it
+        __syncthreads(); // read by all before the next use resets it
         return r;
     }
-    __syncthreads(); // the phase update is seen by all before the next call
+    __syncthreads(); // the phase update is seen by all before the next use
     return -1;
+}
+
+// One chunk through one stage: issue, wait, compare.  Whole CTA.  Returns
+// the first mismatching offset, -1 if none, or -2 when the wait gave up
+// (*err set).
+template <int CH>
+__device__ __noinline__ int64_t stage_scan(const Stage T, const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
+                                           int64_t x0, int64_t y0, int64_t len, unsigned long long *s_min,
+                                           uint64_t spin_ns, uint32_t *err)
+{
+    const StagedChunk K = stage_issue(T, A, n, B, m, x0, y0, len, threadIdx.x == 0);
+    if (!stage_wait(T, spin_ns, err))
+        return -2;
+    return stage_compare(T, K, s_min);
+}
+
+// A[x0 .. x0+lim) against B[y0 ..) chunk by chunk through two stages, the
+// next chunk's copies in flight while the current one is compared.  Whole
+// CTA.  Returns the first mismatching offset, lim if none, or -2 when a
+// wait gave up (*err set).  Before returning it waits for the copies still
+// in flight, so that both stages are idle.
+template <int CH>
+__device__ __noinline__ int64_t stream_scan(const Stage T0, const Stage T1, const uint8_t *A, int64_t n,
+                                            const uint8_t *B, int64_t m, int64_t x0, int64_t y0, int64_t lim,
+                                            unsigned long long *s_min, uint64_t spin_ns, uint32_t *err)
+{
+    const bool lead = threadIdx.x == 0;
+    const int64_t nch = (lim + CH - 1) / CH;
+    StagedChunk K0 = stage_issue(T0, A, n, B, m, x0, y0, min((int64_t)CH, lim), lead);
+    StagedChunk K1{};
+    if (nch > 1)
+        K1 = stage_issue(T1, A, n, B, m, x0 + CH, y0 + CH, min((int64_t)CH, lim - CH), lead);
+    for (int64_t c = 0; c < nch; c++) {
+        const Stage T = (c & 1) ? T1 : T0;
+        const StagedChunk K = (c & 1) ? K1 : K0;
+        if (!stage_wait(T, spin_ns, err))
+            return -2;
+        const int64_t r = stage_compare(T, K, s_min);
+        if (r >= 0) {
+            // the other stage may still be receiving chunk c + 1
+            if (c + 1 < nch && !stage_wait((c & 1) ? T0 : T1, spin_ns, err))
+                return -2;
+            if (c + 1 < nch && lead)
+                *((c & 1) ? T0 : T1).phase ^= 1u;
+            __syncthreads();
+            return c * CH + r;
+        }
+        // this stage is free again: chunk c + 2 goes into it
+        if (c + 2 < nch) {
+            const StagedChunk Kn = stage_issue(T, A, n, B, m, x0 + (c + 2) * CH, y0 + (c + 2) * CH,
+                                               min((int64_t)CH, lim - (c + 2) * CH), lead);
+            if (c & 1)
+                K1 = Kn;
+            else
+                K0 = Kn;
+        }
+    }
+    return lim;
 }
 
 // ------------------------------------------------------- mod 2^61 - 1

@@ -141,7 +141,9 @@ struct LvArgs {
     int32_t help_div;
     // chunks of a long slide its CTA scans alone before publishing the rest
     int32_t local_chunks;
-    // 1: each CTA stages a chunk's bytes in shared memory by bulk copies
+    // stages of shared memory per CTA into which bulk copies bring a long
+    // slide's chunks (0: loads into registers instead; 2: the owner streams
+    // its first chunks with the next one's copies in flight)
     int32_t stage;
 };
 

@@ -218,6 +218,9 @@ struct JobDesc {
 };
 static_assert(sizeof(JobDesc) <= 64, "the job cache fills bytes 192..255 of the smem header");
 
+// Bytes between consecutive stages (128-byte aligned).
+constexpr size_t STAGE_STRIDE = (stage_bytes<CHUNK_BYTES>() + 127) & ~(size_t)127;
+
 // The parts of a chunk's staging at p (128-byte aligned): A side, B side,
 // mbarrier, phase word.
 __device__ __forceinline__ Stage stage_of(unsigned char *p)
@@ -429,6 +432,82 @@ __device__ int claim_loop(const LvArgs &P, const Smem S, JobSlot *sl, int s, uns
     return made;
 }
 
+// claim_loop through two shared-memory stages (budget > 1, P.stage >= 2):
+// each claim's chunk is staged by bulk copies as soon as its claim word is
+// back, while the chunk claimed before it is compared, and the claim after
+// it is in flight meanwhile; so a helper has two chunks' bytes in flight.
+// The same claims, answers and stopping rules as claim_loop.
+__device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, int budget, const Wake *wake)
+{
+    const int tid = threadIdx.x;
+    const Stage T0 = stage_of(S.stg), T1 = stage_of(S.stg + STAGE_STRIDE);
+    unsigned long long wn = 0, bestn = ~0ull; // thread 0: the claim in flight, the result read with it
+    if (tid == 0)
+        wn = atomicAdd(&sl->claim, 1ull);
+    int made = 0, ps = 1;        // ps: the stage holding the pending chunk
+    int pvalid = 0, pgo = 0;     // the pending claim (staged last turn)
+    int64_t pc = 0;
+    for (;;) {
+        const int sn = ps ^ 1;   // the stage for the claim resolved this turn
+        if (tid == 0) {
+            // 1. the claim in flight: valid, worth a scan?
+            const int nv = wn && claim_valid(wn) ? 1 : 0;
+            const int ng = nv ? claim_go(S, sl, s, wn, bestn) : 0;
+            const int64_t nc = (int64_t)(uint32_t)wn;
+            // 2. its copies, in flight while the pending chunk is compared
+            if (ng) {
+                const JobDesc &J = *S.jd;
+                const int64_t cs = nc * (int64_t)CHUNK_BYTES;
+                stage_issue(sn ? T1 : T0, J.A, J.n, J.B, J.m, J.x + cs, J.y + cs,
+                            min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), true);
+            }
+            // 3. the claim after it, in flight meanwhile
+            bool ready = false;
+            if (wake) {
+                const unsigned long long lf = wake->lf ? *(volatile const unsigned long long *)wake->lf : ~0ull;
+                const unsigned long long rf = wake->rf ? *(volatile const unsigned long long *)wake->rf : ~0ull;
+                ready = lf >= wake->want && rf >= wake->want;
+            }
+            const bool more = ng && !ready && made + pvalid + nv < budget;
+            wn = more ? atomicAdd(&sl->claim, 1ull) : 0ull;
+            bestn = more ? *(volatile unsigned long long *)&sl->result : ~0ull;
+            S.bc[0] = nv;
+            S.bc[3] = ng;
+            S.bcl[0] = nc;
+        }
+        __syncthreads();
+        const int nv = S.bc[0], ng = S.bc[3];
+        const int64_t nc = S.bcl[0];
+        __syncthreads();
+        // 4. the pending chunk: compared (when worth it) and answered
+        if (pvalid) {
+            int64_t r = -1;
+            if (pgo) {
+                const JobDesc J = *S.jd;
+                const int64_t cs = pc * (int64_t)CHUNK_BYTES;
+                const Stage T = ps ? T1 : T0;
+                const StagedChunk K = stage_issue(T, J.A, J.n, J.B, J.m, J.x + cs, J.y + cs,
+                                                  min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), false);
+                if (stage_wait(T, P.spin_ns, S.err)) {
+                    const int64_t q = stage_compare(T, K, S.smin);
+                    r = q >= 0 ? cs + q : -1;
+                }
+            }
+            if (tid == 0)
+                answer_claim(sl, pc, r);
+            made++;
+        }
+        // 5. the claim resolved this turn is the pending one now
+        pvalid = nv;
+        pgo = ng;
+        pc = nc;
+        ps = sn;
+        if (!pvalid)
+            break;
+    }
+    return made;
+}
+
 // Help the open jobs of other CTAs (whole CTA): up to `budget` claims on
 // one job.  Returns true if a claim was made.
 __device__ bool help_one(const LvArgs &P, const Smem S, int budget, const Wake *wake = nullptr)
@@ -471,6 +550,8 @@ __device__ bool help_one(const LvArgs &P, const Smem S, int budget, const Wake *
     __syncthreads();
     if (s < 0)
         return false;
+    if (budget > 1 && S.stg && P.stage >= 2)
+        return claim_loop2(P, S, &P.slots[s], s, budget, wake) > 0;
     return claim_loop(P, S, &P.slots[s], s, 0ull, budget, wake) > 0;
 }
 
@@ -631,6 +712,14 @@ __device__ __noinline__ int64_t long_slide(const LvArgs &P, const Smem S, const 
         bulk_prefetch_l2(Q.B, Q.m, y0 + CHUNK_BYTES, loc - CHUNK_BYTES);
     }
     int64_t off = 0;
+    if (S.stg && P.stage >= 2 && loc > CHUNK_BYTES) {
+        // the chunks in turn through two stages, the next one's copies in flight
+        const int64_t r = stream_scan<CHUNK_BYTES>(stage_of(S.stg), stage_of(S.stg + STAGE_STRIDE), Q.A, Q.n, Q.B,
+                                                   Q.m, x0, y0, loc, S.smin, P.spin_ns, S.err);
+        if (r < loc)
+            return r >= 0 ? r : lim0; // (-2: a wait gave up; the launch reports it)
+        off = loc;
+    }
     for (; off < loc; off += CHUNK_BYTES) {
         const int64_t r = chunk_scan(P, S, Q.A, Q.n, Q.B, Q.m, x0 + off, y0 + off, min((int64_t)CHUNK_BYTES, lim0 - off));
         if (r >= 0)
@@ -705,7 +794,7 @@ size_t lv_tiles_smem_bytes(int smax, int h, int stage)
     // two open lists of OCAP (diagonal, start row); DCAP deferred diagonals;
     // then, with a stage, one chunk's bulk-copy staging (128-byte aligned)
     return 256 + 3 * sizeof(int32_t) * ((size_t)smax + 2 * HMAX + 2) +
-           sizeof(int32_t) * (4 * (size_t)OCAP + DCAP) + (stage ? 128 + stage_bytes<CHUNK_BYTES>() : 0);
+           sizeof(int32_t) * (4 * (size_t)OCAP + DCAP) + (stage ? 128 + (size_t)stage * STAGE_STRIDE : 0);
 }
 
 // The frontier of round r (buffers alternate by parity).
@@ -1098,7 +1187,7 @@ __device__ __forceinline__ void lean_slides(const LvArgs &P, const Smem S, const
 }
 
 // Rounds t .. t+h-1 on a narrow tile (the trapezoid, tile and halos, fits
-// one diagonal per thread): every thread computes its diagonal of the round
+// two diagonals per thread): every thread computes its diagonals of the round
 // (start row from the three predecessors, then the word slide); after one
 // barrier the slides the words left open, if any, go to one warp each (up to
 // t2_cap bytes) and then to the whole CTA; every thread then reads the
@@ -1131,8 +1220,7 @@ __device__ __forceinline__ BlockOut run_block_lean(const LvArgs &P, const Smem S
         int32_t *Ld = pr ? S.Ld1 : S.Ld0;
         int32_t *Lc = pr ? S.Lc1 : S.Lc0;
         int *nl = S.nL + pr;
-        const int32_t d = ra + tid;
-        if (d < rb) {
+        for (int32_t d = ra + tid; d < rb; d += (int32_t)blockDim.x) {
             if (d < blo || d > bhi) {
                 cur[d - off] = NEG;
             } else {
@@ -1160,7 +1248,7 @@ __device__ __forceinline__ BlockOut run_block_lean(const LvArgs &P, const Smem S
                             C.mism += (l < full);
                         }
                     } else {
-                        const int j = atomicAdd(nl, 1); // at most one per thread: the list cannot fill
+                        const int j = atomicAdd(nl, 1); // at most two per thread: the list cannot fill
                         Ld[j] = d;
                         Lc[j] = cc;
                         cur[d - off] = PENDING;
@@ -1459,8 +1547,8 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             t = t2;
         } else {
             // ------------------------------------------ h rounds
-            // a trapezoid of at most one diagonal per thread: the lean rounds
-            const BlockOut bo = (b - a) + 2 * h - 2 <= (int64_t)blockDim.x
+            // a trapezoid of at most two diagonals per thread: the lean rounds
+            const BlockOut bo = (b - a) + 2 * h - 2 <= 2 * (int64_t)blockDim.x
                                     ? run_block_lean(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b)
                                     : run_block(P, S, Q, D.dump, D.dump_tmax, D.res, gc, t, h, a, b);
             C.slide += bo.slide;
@@ -1580,12 +1668,13 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         S.jd->jid = 0;
         S.jd->slot = -1;
         *S.jring = 0;
-        if (S.stg) {
-            const Stage T = stage_of(S.stg);
+        for (int i = 0; S.stg && i < P.stage; i++) {
+            const Stage T = stage_of(S.stg + i * STAGE_STRIDE);
             mbar_init(T.bar, 1);
             *T.phase = 0;
-            fence_mbar_init();
         }
+        if (S.stg)
+            fence_mbar_init();
     }
     const uint64_t deadline = gtimer() + P.budget_ns;
     int cls = 0;

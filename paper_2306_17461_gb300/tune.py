@@ -38,14 +38,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # class edges: length buckets and edit-rate buckets of the table
 N_EDGES = [0, 3e6, 3e7, 3e8, 1e12]
 R_EDGES = [0, 3e-6, 3e-5, 3e-4, 1.0]
-DEFAULTS = {"lcp_mode": 1, "block_rounds": 16, "tile_width": 64, "warp_cap": 4096, "local_chunks": 1,
+DEFAULTS = {"lcp_mode": 1, "block_rounds": 16, "tile_width": 64, "warp_cap": 4096, "local_chunks": -1,
             "help_div": 8}
 CANDIDATES = {
     "block_rounds": [4, 8, 16],
     "tile_width": [16, 64, 256],
     "warp_cap": [2048, 4096, 16384],
-    "local_chunks": [-1, 1, 4],
-    "help_div": [-1, 8, 4],
+    "local_chunks": [-1, 2, 8, 32],
+    "help_div": [-1, 8, 4, 2],
     "lcp_mode": [1, 2, 3],
 }
 

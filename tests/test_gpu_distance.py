@@ -25,6 +25,10 @@ CONFIGS = {
     "hash_wide": {"lcp_mode": 2, "tile_width": 1, "block_rounds": 5},
     "bhash": {"lcp_mode": 3},
     "bhash_b7_wide": {"lcp_mode": 3, "hash_block": 7, "tile_width": 1, "block_rounds": 5},
+    # long slides: the CTA scans 4 chunks alone first, half the CTAs serve
+    # slides, a warp hands a slide on after 1 KiB; and no helper CTAs at all
+    "slides_lc4_h2": {"local_chunks": 4, "help_div": 2, "warp_cap": 1024},
+    "no_helpers": {"help_div": -1, "local_chunks": -1},
 }
 
 
