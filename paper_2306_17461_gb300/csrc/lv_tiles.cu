@@ -1240,6 +1240,23 @@ __device__ __forceinline__ BlockOut run_block_lean(const LvArgs &P, const Smem S
                         uint32_t sh;
                         words_load(Q.A, Q.B, n32, m32, cc, d, wa, wb, sh);
                         l = words_lcp(wa, wb, sh, full);
+                        if (l < 0) {
+                            // every byte the words hold matched: 16 more bytes
+                            // of each string in one round trip (the short runs
+                            // inside a burst of edits end here) before the
+                            // slide is listed for a warp
+                            const int32_t k = 8 - (int32_t)max(sh & 255u, sh >> 8);
+                            const uintptr_t pa = (uintptr_t)(Q.A + cc + k), pb = (uintptr_t)(Q.B + (cc + k + d));
+                            const uintptr_t qa = pa & ~(uintptr_t)15, qb = pb & ~(uintptr_t)15;
+                            const uint4 a0 = ld_blk_nb(Q.A, n, qa), a1 = ld_blk_nb(Q.A, n, qa + 16);
+                            const uint4 b0 = ld_blk_nb(Q.B, m, qb), b1 = ld_blk_nb(Q.B, m, qb + 16);
+                            const int32_t f = first_diff16(shift_bytes(a0, a1, (uint32_t)(pa & 15)),
+                                                           shift_bytes(b0, b1, (uint32_t)(pb & 15)));
+                            if (k + f >= full)
+                                l = full;
+                            else if (f < 16)
+                                l = k + f;
+                        }
                     }
                     if (l >= 0) {
                         cur[d - off] = cc + l;
