@@ -540,7 +540,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
         (r = ensure(ctx, ctx->ctl, sizeof(LaunchCtl))) != ED_OK ||
         (r = ensure(ctx, ctx->gctl, sizeof(GroupCtl) * ngroups)) != ED_OK ||
         (r = ensure(ctx, ctx->slots, sizeof(JobSlot) * grid * JOB_RING)) != ED_OK ||
-        (r = ensure(ctx, ctx->halo, sizeof(int32_t) * (size_t)grid * 4 * HMAX)) != ED_OK ||
+        (r = ensure(ctx, ctx->halo, sizeof(unsigned long long) * (size_t)grid * 4 * HMAX)) != ED_OK ||
         (r = ensure(ctx, ctx->pdesc, sizeof(PairDesc) * np)) != ED_OK ||
         (r = ensure(ctx, ctx->res, sizeof(unsigned long long) * R_COUNT * np)) != ED_OK)
         return r;
@@ -577,7 +577,7 @@ static int run_tiles_once(ed_ctx *ctx, const std::vector<TileJob> &jobs, cudaStr
     P.gctl = (GroupCtl *)ctx->gctl.p;
     P.ctl = (LaunchCtl *)ctx->ctl.p;
     P.slots = (JobSlot *)ctx->slots.p;
-    P.halo = (int32_t *)ctx->halo.p;
+    P.halo = (unsigned long long *)ctx->halo.p;
     P.gf = (int32_t *)ctx->gf.p;
     P.kcap = (int32_t)kcap;
     P.smax = (int32_t)smax;

@@ -80,8 +80,6 @@ struct __align__(64) LaunchCtl {
     // values seen, done_k
     unsigned long long diag[8];
     unsigned long long active[(MAX_GRID * JOB_RING + 63) / 64]; // job slots open for help
-    // per CTA: (pair iteration << 32) | first round not yet published
-    unsigned long long flags[MAX_GRID];
 };
 
 // Result counters written by a launch, per pair.
@@ -119,7 +117,8 @@ struct LvArgs {
     GroupCtl *gctl;
     LaunchCtl *ctl;
     JobSlot *slots;       // gridDim.x * JOB_RING slots (CTA c owns c * JOB_RING ..)
-    int32_t *halo;        // [gridDim.x][2 parity][2 sides][HMAX]
+    // tile edges: [gridDim.x][2 parity][2 sides][HMAX] words (round << 32) | L
+    unsigned long long *halo;
     int32_t *gf;
     int32_t kcap;         // round cap (largest epoch radius)
     int32_t smax;         // tile width capacity (shared memory)

@@ -18,23 +18,23 @@
 //  * Temporal blocking: a CTA holds its tile plus h diagonals of halo on
 //    each side and runs h rounds on the shrinking trapezoid (the halo
 //    diagonals are recomputed, exactly), then trades its h edge values with
-//    its two neighbours through global memory and a per-CTA release flag.
-//    There is no grid-wide barrier per round, only neighbour waits every h
-//    rounds.
-//  * Pipelined rounds: within a block, six warps compute round t while two
-//    slider warps finish the open slides of round t - 1 and then the
-//    diagonals beside them; two CTA barriers a round (run_block).
+//    its two neighbours through global memory, each value in one 8-byte word
+//    with its round (no fence, no flag).  There is no grid-wide barrier per
+//    round, only neighbour waits every h rounds.
+//  * Rounds: a narrow trapezoid (two diagonals per thread at most) runs the
+//    lean form, one CTA barrier a round (run_block_lean); a wide one runs
+//    pipelined rounds, six warps computing round t while two slider warps
+//    finish the open slides of round t - 1 and the diagonals beside them
+//    (run_block).
 //  * Slides: one thread compares the two aligned 4-byte words at each start
-//    row (at least five bytes; several diagonals' loads in flight
-//    together); slides that match all of them go to one warp each (ballot /
-//    first set bit over 2 KiB steps, prefetching the next 4 KiB into L2 when
-//    done, where the next round starts), then, if still open after t2_cap
-//    bytes, to the whole CTA, which scans 64 KiB per step with every load in
-//    flight (after one bulk L2 prefetch of what it scans).  A slide still open
-//    after LOCAL_STEPS such steps becomes a job in the CTA's job slot: its
-//    64 KiB chunks are claimed by atomicAdd by the owner and by every CTA
-//    that is waiting on a neighbour or has no tile; the first mismatch is the
-//    atomicMin over chunks.
+//    row (at least five bytes; several diagonals' loads in flight together;
+//    in the lean form 16 more bytes in one round trip when they all match);
+//    slides still open go to one warp each (ballot / first set bit over
+//    2 KiB steps), then, past t2_cap bytes, to the whole CTA, which opens a
+//    job in its job slot: 16 KiB chunks (of each string), chunk 0 scanned by
+//    the owner, the others claimed in order by atomicAdd by every CTA that is
+//    waiting on a neighbour or has no tile, each staged in shared memory by
+//    bulk copies; the first mismatch is the least over the chunks.
 //  * Every wait is bounded by %globaltimer and reports ST_TIMEOUT (with the
 //    place it gave up) instead of hanging.
 #include "ed_device.cuh"
@@ -45,6 +45,16 @@ namespace edg {
 
 constexpr int64_t GROW_NUM = 9, GROW_DEN = 8; // epoch radius growth factor
 constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
+// Polls of the edge words by warp 0 before the CTA looks at anything else.
+constexpr int HALO_SPINS = 4;
+// Looks at the job slots by thread 0 of a CTA without a tile before its
+// CTA meets at a barrier.
+constexpr int IDLE_SPINS = 32;
+// Looks at its job by the owner's warp 0 before its CTA meets at a barrier,
+// and how long the claim count may stand still before the owner scans a
+// chunk itself.
+constexpr int WATCH_SPINS = 8;
+constexpr uint64_t OWN_SCAN_NS = 1000;
 
 struct Counters {
     unsigned long long slide = 0, mism = 0, hashq = 0, coll = 0, longs = 0, blocks = 0, opens = 0;
@@ -178,6 +188,16 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v)
+{
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 // Orders the relaxed loads before it ahead of every access after it (the
 // acquire half of a flag handshake whose writer used a release).
@@ -373,12 +393,19 @@ __device__ __forceinline__ void scan_claim(const LvArgs &P, const Smem S, JobSlo
         answer_claim(sl, c, r);
 }
 
-// What ends a CTA's helping early: both neighbours' flags (null: none) at
-// `want` or beyond, i.e. the CTA's own next block can start.
+// What ends a CTA's helping early: the first edge word of both neighbours
+// (null: none) at round `want` or beyond, i.e. the CTA's own next block can
+// (most likely) start.
 struct Wake {
-    const unsigned long long *lf, *rf;
-    unsigned long long want;
+    const unsigned long long *lw, *rw;
+    uint32_t want;
 };
+__device__ __forceinline__ bool wake_ready(const Wake *w)
+{
+    const unsigned long long a = w->lw ? ld_relaxed_u64(w->lw) : ~0ull;
+    const unsigned long long b = w->rw ? ld_relaxed_u64(w->rw) : ~0ull;
+    return (uint32_t)(a >> 32) >= w->want && (uint32_t)(b >> 32) >= w->want;
+}
 
 // The whole CTA claims and scans chunks of slot s's job, in order, up to
 // `budget` claims: thread 0 makes the next claim before the current chunk
@@ -399,12 +426,7 @@ __device__ int claim_loop(const LvArgs &P, const Smem S, JobSlot *sl, int s, uns
     int made = 0;
     for (;;) {
         if (tid == 0) {
-            bool ready = false;
-            if (wake) {
-                const unsigned long long lf = wake->lf ? *(volatile const unsigned long long *)wake->lf : ~0ull;
-                const unsigned long long rf = wake->rf ? *(volatile const unsigned long long *)wake->rf : ~0ull;
-                ready = lf >= wake->want && rf >= wake->want;
-            }
+            const bool ready = wake && wake_ready(wake);
             const int valid = claim_valid(w) ? 1 : 0;
             const int go = valid ? claim_go(S, sl, s, w, best) : 0;
             S.bc[0] = valid;
@@ -462,12 +484,7 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
                             min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), true);
             }
             // 3. the claim after it, in flight meanwhile
-            bool ready = false;
-            if (wake) {
-                const unsigned long long lf = wake->lf ? *(volatile const unsigned long long *)wake->lf : ~0ull;
-                const unsigned long long rf = wake->rf ? *(volatile const unsigned long long *)wake->rf : ~0ull;
-                ready = lf >= wake->want && rf >= wake->want;
-            }
+            const bool ready = wake && wake_ready(wake);
             const bool more = ng && !ready && made + pvalid + nv < budget;
             wn = more ? atomicAdd(&sl->claim, 1ull) : 0ull;
             bestn = more ? *(volatile unsigned long long *)&sl->result : ~0ull;
@@ -508,51 +525,58 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
     return made;
 }
 
-// Help the open jobs of other CTAs (whole CTA): up to `budget` claims on
-// one job.  Returns true if a claim was made.
-__device__ bool help_one(const LvArgs &P, const Smem S, int budget, const Wake *wake = nullptr)
+// Thread 0: an open job slot of another CTA, or -1.  The active bitmask
+// over the slots (its first eight words loaded together) is read from a
+// CTA-dependent bit on, so that helpers spread over jobs.
+__device__ __forceinline__ int pick_slot(const LvArgs &P)
 {
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        int s = -1;
-        // the active bitmask over the job slots (its first eight words loaded
-        // together), from a CTA-dependent bit so that helpers spread over jobs
-        const int nslot = (int)gridDim.x * JOB_RING;
-        const int nw = (nslot + 63) >> 6;
-        const volatile unsigned long long *act = P.ctl->active;
-        unsigned long long b[8];
+    int s = -1;
+    const int nslot = (int)gridDim.x * JOB_RING;
+    const int nw = (nslot + 63) >> 6;
+    const volatile unsigned long long *act = P.ctl->active;
+    unsigned long long b[8];
 #pragma unroll
-        for (int k = 0; k < 8; k++)
-            b[k] = k < nw ? act[k] : 0ull;
-        const int rot = blockIdx.x & 63;
-        const int w0 = (int)(((int)blockIdx.x * JOB_RING / 64) % nw);
-        for (int k = 0; k < nw && s < 0; k++) {
-            const int wd = (w0 + k) % nw;
-            unsigned long long v = 0ull;
+    for (int k = 0; k < 8; k++)
+        b[k] = k < nw ? act[k] : 0ull;
+    const int rot = blockIdx.x & 63;
+    const int w0 = (int)(((int)blockIdx.x * JOB_RING / 64) % nw);
+    for (int k = 0; k < nw && s < 0; k++) {
+        const int wd = (w0 + k) % nw;
+        unsigned long long v = 0ull;
 #pragma unroll
-            for (int q = 0; q < 8; q++)
-                if (wd == q)
-                    v = b[q];
-            if (wd >= 8)
-                v = act[wd];
-            v = (v >> rot) | (rot ? (v << (64 - rot)) : 0ull);
-            while (v && s < 0) {
-                const int j = wd * 64 + ((__ffsll((long long)v) - 1 + rot) & 63);
-                v &= v - 1;
-                if (j < nslot && j / JOB_RING != (int)blockIdx.x)
-                    s = j;
-            }
+        for (int q = 0; q < 8; q++)
+            if (wd == q)
+                v = b[q];
+        if (wd >= 8)
+            v = act[wd];
+        v = (v >> rot) | (rot ? (v << (64 - rot)) : 0ull);
+        while (v && s < 0) {
+            const int j = wd * 64 + ((__ffsll((long long)v) - 1 + rot) & 63);
+            v &= v - 1;
+            if (j < nslot && j / JOB_RING != (int)blockIdx.x)
+                s = j;
         }
-        S.bc[1] = s;
     }
-    __syncthreads();
-    const int s = S.bc[1];
-    __syncthreads();
-    if (s < 0)
-        return false;
+    return s;
+}
+
+// The whole CTA claims and scans chunks of slot s's job (s >= 0), up to
+// `budget` claims.  Returns true if a claim was made.
+__device__ __forceinline__ bool serve_slot(const LvArgs &P, const Smem S, int s, int budget, const Wake *wake)
+{
     if (budget > 1 && S.stg && P.stage >= 2)
         return claim_loop2(P, S, &P.slots[s], s, budget, wake) > 0;
     return claim_loop(P, S, &P.slots[s], s, 0ull, budget, wake) > 0;
+}
+
+// Whether mark word w (chunks 64w .. 64w+63) marks every chunk below need.
+__device__ __forceinline__ bool marks_cover(unsigned long long mw, uint32_t w, uint32_t need)
+{
+    if (w * 64 >= need)
+        return true;
+    const uint32_t hi = min(need - w * 64, 64u);
+    const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
+    return (mw & want) == want;
 }
 
 // One job of the CTA's long slide (whole CTA): the first mismatch of
@@ -646,35 +670,46 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     __syncthreads();
     claim_loop(P, S, sl, sidx, w0, 1, nullptr, (unsigned long long)lim); // chunk 0 (no mismatch known yet)
     // ------------------------------------------------ watch
-    // warp 0 looks at the marks (acquire), then at the result and the claim
-    // count: final once every chunk up to the one holding the best mismatch
-    // is answered; with no claim made since the last look (no helper at
-    // hand), the CTA scans a chunk itself
+    // warp 0 looks at the result, the claim count and the marks together
+    // (several looks before the CTA meets at a barrier): final once every
+    // chunk up to the one holding the best mismatch is marked answered, the
+    // result then read again after an acquire fence (every mismatch of a
+    // chunk seen answered is in it).  With no claim by another CTA for
+    // OWN_SCAN_NS (no helper at hand), the CTA scans a chunk itself.
+    static_assert(JOB_MAX_CHUNKS <= 64 * 64, "two mark words per lane");
     uint32_t last = 1;
+    uint64_t tnew = gtimer(); // lane 0: when the claim count last moved
     for (;;) {
         if (tid < 32) {
-            const unsigned long long best0 = *(volatile unsigned long long *)&sl->result;
-            const uint32_t cs = best0 < (unsigned long long)lim ? (uint32_t)(best0 / CHUNK_BYTES) : nch - 1;
-            const uint32_t need = min(cs + 1, nch);
-            bool ok = true;
-            for (uint32_t w = lane; w * 64 < need; w += 32) {
-                const uint32_t hi = min(need - w * 64, 64u);
-                const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
-                ok &= ((*(volatile unsigned long long *)&sl->bits[w]) & want) == want;
-            }
-            fence_acquire();
-            ok = __all_sync(0xffffffffu, ok);
-            if (lane == 0) {
-                // the result after the marks: every mismatch of a chunk seen
-                // answered is in it
-                const unsigned long long best = *(volatile unsigned long long *)&sl->result;
+            int act = 0; // 0 look again, 1 scan a chunk, 2 final
+            unsigned long long best = 0;
+            for (int spin = 0; spin < WATCH_SPINS && act == 0; spin++) {
+                const unsigned long long best0 = *(volatile unsigned long long *)&sl->result;
                 const uint32_t cnt = (uint32_t)*(volatile unsigned long long *)&sl->claim & ~CLAIM_CLOSE;
-                int act = 0; // 0 look again, 1 scan a chunk, 2 final
-                if (ok && best <= best0)
+                const uint32_t w0 = (uint32_t)lane, w1 = (uint32_t)lane + 32;
+                const unsigned long long m0 = w0 * 64 < nch ? *(volatile unsigned long long *)&sl->bits[w0] : 0ull;
+                const unsigned long long m1 = w1 * 64 < nch ? *(volatile unsigned long long *)&sl->bits[w1] : 0ull;
+                const uint32_t cs = best0 < (unsigned long long)lim ? (uint32_t)(best0 / CHUNK_BYTES) : nch - 1;
+                const uint32_t need = min(cs + 1, nch);
+                const bool ok = __all_sync(0xffffffffu, marks_cover(m0, w0, need) && marks_cover(m1, w1, need));
+                if (ok) {
+                    fence_acquire();
+                    if (lane == 0)
+                        best = *(volatile unsigned long long *)&sl->result;
                     act = 2;
-                else if (cnt == last && cnt < nch)
-                    act = 1;
-                last = cnt;
+                } else if (lane == 0) {
+                    const uint64_t now = gtimer();
+                    if (cnt != last) {
+                        last = cnt;
+                        tnew = now;
+                    } else if (cnt < nch && now - tnew > OWN_SCAN_NS) {
+                        act = 1;
+                        last = cnt + 1; // the CTA's own claim
+                    }
+                }
+                act = __shfl_sync(0xffffffffu, act, 0);
+            }
+            if (lane == 0) {
                 S.bc[5] = act;
                 S.bcl[1] = (long long)best;
             }
@@ -874,7 +909,17 @@ __device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int g
     return T;
 }
 
-__device__ __forceinline__ int32_t *halo_ptr(const LvArgs &P, int cta, int parity, int side)
+// A tile's edge values of round t - 1 for its neighbours, one word each:
+// (t << 32) | L in a single 8-byte store, so that a reader that sees the
+// round sees the value with it (no fence, no flag).  Parity (t / h) & 1
+// alternates the buffers: a tile can be one block ahead of its neighbour at
+// most, so it never overwrites a word its neighbour has still to read.
+__device__ __forceinline__ unsigned long long halo_word(uint32_t t, int32_t v)
+{
+    return ((unsigned long long)t << 32) | (uint32_t)v;
+}
+
+__device__ __forceinline__ unsigned long long *halo_ptr(const LvArgs &P, int cta, int parity, int side)
 {
     return P.halo + ((int64_t)(cta * 2 + parity) * 2 + side) * HMAX;
 }
@@ -1342,7 +1387,7 @@ __device__ void pair_stop(const PairDesc &D, GroupCtl *gc, uint32_t status)
 // Runs one pair on the group; kc is the radius its re-tiling buffers hold.
 // Returns false if the launch must stop.
 __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const PairDesc &D, GroupCtl *gc, int gi, int G,
-                         int c0, int32_t *gfb, int64_t kc, unsigned long long iter, uint64_t deadline,
+                         int c0, int32_t *gfb, int64_t kc, uint64_t deadline,
                          Counters &C)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -1416,32 +1461,43 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             ((t + h - 1 > R) && (R < nm)) || (can_suspend && t >= t_ep + P.sync_rounds);
         if (!T.has && !need_change) {
             // no tile: help open slides until the epoch changes or k is found
+            // (thread 0 looks at the group's words and the job slots together,
+            // several times before the CTA meets at a barrier)
             uint64_t t0 = tid == 0 ? gtimer() : 0;
             for (;;) {
                 if (tid == 0) {
-                    // the three words at once (relaxed); an acquire fence
-                    // before epoch_t is read
-                    const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
-                    const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
-                    const uint32_t eq = *(volatile uint32_t *)&gc->epoch_req;
-                    int st = 0;
-                    if (dk != ~0ull)
-                        st = 1;
-                    else if (er != 0)
-                        st = 2;
-                    else if (eq > epoch) {
-                        fence_acquire();
-                        st = 3;
-                    } else if (gtimer() - t0 > P.idle_ns) {
-                        wait_failed(P, 3, t, epoch, ld_acquire(&gc->epoch_req), R, T.ntiles);
-                        st = 2;
+                    int st = 0, sl = -1;
+                    for (int spin = 0; spin < IDLE_SPINS && st == 0 && sl < 0; spin++) {
+                        const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
+                        const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
+                        const uint32_t eq = *(volatile uint32_t *)&gc->epoch_req;
+                        const uint32_t ec = *(volatile uint32_t *)&gc->ebar_count;
+                        const int js = pick_slot(P);
+                        // a job of the group is served even once the epoch
+                        // change is asked for, until every tile is at the
+                        // barrier (no job of the group opens after that)
+                        const bool mine = js >= 0 && js / JOB_RING >= c0 && js / JOB_RING < c0 + G;
+                        if (dk != ~0ull)
+                            st = 1;
+                        else if (er != 0)
+                            st = 2;
+                        else if (js >= 0 && (eq <= epoch || (mine && ec < (uint32_t)T.ntiles)))
+                            sl = js;
+                        else if (eq > epoch && ec >= (uint32_t)T.ntiles) {
+                            fence_acquire(); // before epoch_t is read
+                            st = 3;
+                        } else if (gtimer() - t0 > P.idle_ns) {
+                            wait_failed(P, 3, t, epoch, ld_acquire(&gc->epoch_req), R, T.ntiles);
+                            st = 2;
+                        }
                     }
                     S.bc[1] = st;
+                    S.bc[2] = sl;
                     if (st == 3)
                         S.bcl[2] = *(volatile uint32_t *)&gc->epoch_t;
                 }
                 __syncthreads();
-                const int st = S.bc[1];
+                const int st = S.bc[1], sl = S.bc[2];
                 const int64_t et = S.bcl[2];
                 __syncthreads();
                 if (st == 1)
@@ -1452,8 +1508,8 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                     t = et;
                     break;
                 }
-                if (!help_one(P, S, 8))
-                    __nanosleep(256);
+                if (sl >= 0)
+                    serve_slot(P, S, sl, 8, nullptr);
             }
         }
         const bool grow = (t + h - 1 > R) && (R < nm);
@@ -1558,8 +1614,8 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 f[d - off] = NEG;
             const int op = (int)(((t2 / h) & 1) ^ 1);
             if (tid < h) {
-                st_cg(halo_ptr(P, blockIdx.x, op, 0) + tid, NEG);
-                st_cg(halo_ptr(P, blockIdx.x, op, 1) + tid, NEG);
+                st_relaxed_u64(halo_ptr(P, blockIdx.x, op, 0) + tid, halo_word((uint32_t)(t2 - h), NEG));
+                st_relaxed_u64(halo_ptr(P, blockIdx.x, op, 1) + tid, halo_word((uint32_t)(t2 - h), NEG));
             }
             t = t2;
         } else {
@@ -1583,51 +1639,65 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             C.blocks++;
         }
         // ---------------------------------------------- halo exchange
+        // The edge words of round t - 1 (halo_word): a word of round t or
+        // later is the value for round t - 1 (a later round is a tile that
+        // skipped ahead with minus infinity on its edges, which holds for the
+        // rounds it skipped as well).
         const uint64_t tw0 = clock64();
         const int parity = (int)((t / h) & 1);
-        const int32_t *last = frontier(S, t - 1);
-        int32_t *hl = halo_ptr(P, blockIdx.x, parity, 0), *hr = halo_ptr(P, blockIdx.x, parity, 1);
+        int32_t *edge = frontier(S, t - 1);
+        const uint32_t tag = (uint32_t)t;
         if (tid < h) {
             const int64_t dl = a + tid, dr = b - h + tid;
-            st_cg(hl + tid, dl < b ? last[dl - off] : NEG);
-            st_cg(hr + tid, dr >= a ? last[dr - off] : NEG);
+            st_relaxed_u64(halo_ptr(P, blockIdx.x, parity, 0) + tid, halo_word(tag, dl < b ? edge[dl - off] : NEG));
+            st_relaxed_u64(halo_ptr(P, blockIdx.x, parity, 1) + tid, halo_word(tag, dr >= a ? edge[dr - off] : NEG));
         }
-        __threadfence();
-        __syncthreads();
-        const unsigned long long want = (iter << 32) | (unsigned long long)t;
-        if (tid == 0)
-            st_release_u64(&P.ctl->flags[blockIdx.x], want);
-        // wait for both neighbours, helping open slides meanwhile
+        const unsigned long long *lw = T.left >= 0 ? halo_ptr(P, T.left, parity, 1) : nullptr;
+        const unsigned long long *rw = T.right >= 0 ? halo_ptr(P, T.right, parity, 0) : nullptr;
+        // wait for both neighbours' words (warp 0: lanes 0..15 the left
+        // neighbour's, 16..31 the right one's), helping open slides meanwhile
         const uint64_t t0 = tid == 0 ? gtimer() : 0;
         for (;;) {
-            if (tid == 0) {
-                // every word at once (relaxed loads), then an acquire fence
-                // once both neighbours' flags are up: their halo values are
-                // read after it
-                const unsigned long long lf =
-                    T.left >= 0 ? *(volatile unsigned long long *)&P.ctl->flags[T.left] : ~0ull;
-                const unsigned long long rf =
-                    T.right >= 0 ? *(volatile unsigned long long *)&P.ctl->flags[T.right] : ~0ull;
-                const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
-                const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
-                int st = 0;
-                if (lf >= want && rf >= want) {
-                    fence_acquire();
-                    st = 3;
-                } else if (pair_over_seen(D, dk, t))
-                    st = 1;
-                else if (er != 0)
-                    st = 2;
-                else if (gtimer() - t0 > P.idle_ns) {
-                    wait_failed(P, 4, t, want, T.left >= 0 ? ld_acquire_u64(&P.ctl->flags[T.left]) : ~0ull,
-                                T.right >= 0 ? ld_acquire_u64(&P.ctl->flags[T.right]) : ~0ull,
-                                ((unsigned long long)(uint32_t)T.left << 32) | (uint32_t)T.right);
-                    st = 2;
+            if (tid < 32) {
+                const int side = tid >> 4, j = tid & 15;
+                const unsigned long long *wp = side ? rw : lw;
+                int st = 0, js = -1;
+                for (int spin = 0; spin < HALO_SPINS; spin++) {
+                    const unsigned long long v = (j < h && wp) ? ld_relaxed_u64(wp + j) : ~0ull;
+                    // an open job of another CTA, looked for in the same round trip
+                    int q = tid == 0 ? pick_slot(P) : -1;
+                    if (__all_sync(0xffffffffu, (uint32_t)(v >> 32) >= tag)) {
+                        if (j < h)
+                            edge[(side ? b + j : a - h + j) - off] = wp ? (int32_t)(uint32_t)v : NEG;
+                        st = 3;
+                        break;
+                    }
+                    q = __shfl_sync(0xffffffffu, q, 0);
+                    if (q >= 0) {
+                        js = q;
+                        break;
+                    }
                 }
-                S.bc[1] = st;
+                if (tid == 0 && st == 0 && js < 0) {
+                    const unsigned long long dk = *(volatile unsigned long long *)&gc->done_k;
+                    const uint32_t er = *(volatile uint32_t *)&P.ctl->error;
+                    if (pair_over_seen(D, dk, t))
+                        st = 1;
+                    else if (er != 0)
+                        st = 2;
+                    else if (gtimer() - t0 > P.idle_ns) {
+                        wait_failed(P, 4, t, tag, lw ? ld_relaxed_u64(lw) : ~0ull, rw ? ld_relaxed_u64(rw) : ~0ull,
+                                    ((unsigned long long)(uint32_t)T.left << 32) | (uint32_t)T.right);
+                        st = 2;
+                    }
+                }
+                if (tid == 0) {
+                    S.bc[1] = st;
+                    S.bc[2] = js;
+                }
             }
             __syncthreads();
-            const int st = S.bc[1];
+            const int st = S.bc[1], js = S.bc[2];
             __syncthreads();
             if (st == 1)
                 return true;
@@ -1635,16 +1705,11 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 return false;
             if (st == 3)
                 break;
-            const Wake wk{T.left >= 0 ? &P.ctl->flags[T.left] : nullptr,
-                          T.right >= 0 ? &P.ctl->flags[T.right] : nullptr, want};
-            help_one(P, S, 16, &wk);
+            if (js >= 0) {
+                const Wake wk{lw, rw, tag};
+                serve_slot(P, S, js, 16, &wk);
+            }
         }
-        int32_t *edge = frontier(S, t - 1);
-        if (tid < h) {
-            edge[a - h + tid - off] = T.left >= 0 ? ld_cg(halo_ptr(P, T.left, parity, 1) + tid) : NEG;
-            edge[b + tid - off] = T.right >= 0 ? ld_cg(halo_ptr(P, T.right, parity, 0) + tid) : NEG;
-        }
-        __syncthreads();
         C.tm[2] += clock64() - tw0;
     }
 }
@@ -1704,7 +1769,13 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
     const int64_t kc = P.cls_kc[cls];
     int32_t *gfb = P.gf + P.cls_gf[cls] + (int64_t)(rel / G) * 2 * (2 * kc + 5);
     Counters C;
-    for (unsigned long long iter = 1;; iter++) {
+    for (;;) {
+        // the CTA's edge words start each pair cleared (round 0): every CTA
+        // of the group has left the pair before (the barrier that ends the
+        // last turn), and the barrier below orders the clear before the
+        // first read of the next pair
+        for (int i = threadIdx.x; i < 4 * HMAX; i += blockDim.x)
+            st_relaxed_u64(P.halo + (size_t)blockIdx.x * 4 * HMAX + i, 0ull);
         if (gi == 0 && threadIdx.x == 0) {
             // the class's own queue first, then the classes below it
             int32_t q = -1;
@@ -1729,7 +1800,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         if (q < 0)
             break;
         const PairDesc D = P.pairs[q];
-        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, iter, deadline, C);
+        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, deadline, C);
         flush_counters(D, C, gi == 0);
         if (!ok)
             break;

@@ -38,7 +38,7 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable(orc):
         assert ei.value.code == ed.ED_ETIMEOUT, str(ei.value)
         m = re.search(r"kernel check failed: site (\d+) cta (\d+) t (\d+)", str(ei.value))
         assert m, str(ei.value)
-        # 1 job close, 2 group barrier, 3 idle CTA, 4 neighbour flags, 5 epoch barrier
+        # 1 job close, 2 group barrier, 3 idle CTA, 4 neighbours' edge words, 5 epoch barrier
         assert 1 <= int(m.group(1)) <= 5
     finally:
         c.close()
