@@ -599,7 +599,11 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     const int word = sidx >> 6;
     const unsigned long long bit = 1ull << (sidx & 63);
     // ------------------------------------------------ reuse of the slot
-    if (tid < 32) {
+    // (skipped when the CTA's previous job already checked it and cleared its
+    // marks: prep[ring])
+    int *prep = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 120);
+    const bool ready = prep[ring] != 0;
+    if (tid < 32 && !ready) {
         // every claim of the slot's last job answered, and its marks seen
         // (the claims made before its close; 0 for a slot not used yet)
         const uint32_t cnt = sl->nvalid;
@@ -626,7 +630,7 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     }
     // warp 0 clears the marks the job will use (each lane fenced before the
     // barrier, so that the release below orders them before the job opens)
-    if (tid < 32) {
+    if (tid < 32 && !ready) {
         for (uint32_t w = tid; w * 64 < nch; w += 32)
             sl->bits[w] = 0ull;
         __threadfence();
@@ -634,6 +638,7 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     __syncthreads();
     // ------------------------------------------------ publish
     if (tid == 0) {
+        prep[ring] = 0;
         *S.jring = (ring + 1) % JOB_RING;
         sl->A = Q.A;
         sl->B = Q.B;
@@ -679,6 +684,7 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     static_assert(JOB_MAX_CHUNKS <= 64 * 64, "two mark words per lane");
     uint32_t last = 1;
     uint64_t tnew = gtimer(); // lane 0: when the claim count last moved
+    bool first = true;        // warp 1: the other slot still to prepare
     for (;;) {
         if (tid < 32) {
             int act = 0; // 0 look again, 1 scan a chunk, 2 final
@@ -712,6 +718,27 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
             if (lane == 0) {
                 S.bc[5] = act;
                 S.bcl[1] = (long long)best;
+            }
+        } else if (tid < 64 && first) {
+            // warp 1, once: the CTA's other slot (its next job's) -- every
+            // claim of the job it held answered and marked -- gets its marks
+            // cleared now, off the next job's path
+            first = false;
+            const int o = (ring + 1) % JOB_RING;
+            JobSlot *so = &P.slots[(int)blockIdx.x * JOB_RING + o];
+            const uint32_t cnt = so->nvalid;
+            const uint32_t need = min(cnt, (uint32_t)JOB_MAX_CHUNKS);
+            bool ok = true;
+            for (uint32_t w = lane; w * 64 < need; w += 32)
+                ok &= marks_cover(*(volatile unsigned long long *)&so->bits[w], w, need);
+            ok = __all_sync(0xffffffffu, ok) && *(volatile unsigned int *)&so->done >= cnt;
+            if (ok) {
+                for (uint32_t w = lane; w < JOB_MAX_CHUNKS / 64; w += 32)
+                    so->bits[w] = 0ull;
+                __threadfence();
+                __syncwarp();
+                if (lane == 0)
+                    prep[o] = 1;
             }
         }
         __syncthreads();
@@ -851,6 +878,7 @@ __device__ Smem carve(const LvArgs &P)
     S.nR = S.nL + 7;
     S.jd = reinterpret_cast<JobDesc *>(p + 192);
     S.jring = reinterpret_cast<int *>(p + 48);
+    // p + 168 .. p + 176: prep[JOB_RING] (run_job); p + 176: lone (lean_slides)
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -1215,19 +1243,33 @@ __device__ __forceinline__ BlockOut run_block(const LvArgs &P, const Smem S, con
 
 // The open slides of a lean round (out of line: most rounds have none):
 // one warp each, up to t2_cap bytes, then the whole CTA for those still
-// open.  Every thread calls it; the final rows are visible to every thread
-// when it returns.
+// open -- or, for a lone slide after a lone one that outran its warp, the
+// whole CTA at once.  Every thread calls it (after a barrier); the final
+// rows are visible to every thread when it returns.
 __device__ __forceinline__ void lean_slides(const LvArgs &P, const Smem S, const Pair Q, int32_t *cur, int64_t off,
                                          int32_t *Ld, const int32_t *Lc, int nlo, int64_t a, int64_t b, int pr,
                                          Counters &C)
 {
-    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    warp_slides(P, Q, cur, off, Ld, Lc, nlo, a, b, warp, nw, C, S.left + pr);
-    __syncthreads();
-    if (S.left[pr])
+    // lone: whether the CTA's last lone slide outran one warp (t2_cap bytes);
+    // the next lone one then goes to the whole CTA at once (its job opens
+    // without the warp's step first): on the alignment path, slides long
+    // and short come in runs
+    int *lone = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 128);
+    const bool direct = nlo == 1 && *lone != 0;
+    if (direct) {
         cta_slides(P, S, Q, cur, off, Ld, Lc, nlo, a, b, C);
-    if (threadIdx.x == 0)
+    } else {
+        const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        warp_slides(P, Q, cur, off, Ld, Lc, nlo, a, b, warp, nw, C, S.left + pr);
+        __syncthreads();
+        if (S.left[pr])
+            cta_slides(P, S, Q, cur, off, Ld, Lc, nlo, a, b, C);
+    }
+    if (threadIdx.x == 0) {
+        if (nlo == 1)
+            *lone = direct ? (cur[Ld[0] - off] - Lc[0] > P.t2_cap) : S.left[pr];
         S.left[pr] = 0;
+    }
     __syncthreads();
 }
 
@@ -1519,26 +1561,30 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             const uint64_t te0 = clock64();
             int64_t Rn = R;
             bool wide = false; // the band outgrew the tiles: save it for wider ones
+            // the round cap, or tiles too narrow with nowhere to save the band:
+            // the pair stops here -- but only once every CTA of the group has
+            // reached this round without k being found (a CTA may run blocks
+            // ahead of the one that finds k), so the decision waits for the
+            // barrier below
+            uint32_t stop = 0;
             if (grow) {
                 Rn = min(max(R * GROW_NUM / GROW_DEN, t + h - 1), min(nm, (int64_t)P.kcap));
-                if (t + h - 1 > Rn && Rn < nm) {
-                    pair_stop(D, gc, ST_LIMIT);
-                    return true;
-                }
+                if (t + h - 1 > Rn && Rn < nm)
+                    stop = ST_LIMIT;
                 // no further than the group's tiles (and the keep buffer) hold
                 Rn = min(Rn, fit_radius(n, m, (int64_t)G * P.smax));
                 if (D.keep)
                     Rn = min(Rn, D.keep_r);
-                if (t + h - 1 > Rn && Rn < nm) {
-                    if (!D.keep) {
-                        pair_stop(D, gc, ST_WIDE);
-                        return true;
+                if (!stop && t + h - 1 > Rn && Rn < nm) {
+                    if (!D.keep)
+                        stop = ST_WIDE;
+                    else {
+                        // every CTA of the group takes this decision at the same
+                        // round: the band of round t - 1 is saved below as for a
+                        // time slice, and the host resumes the pair on wider tiles
+                        wide = true;
+                        Rn = R;
                     }
-                    // every CTA of the group takes this decision at the same
-                    // round: the band of round t - 1 is saved below as for a
-                    // time slice, and the host resumes the pair on wider tiles
-                    wide = true;
-                    Rn = R;
                 }
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
@@ -1560,6 +1606,10 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 return false;
             if (eb == 2)
                 return true; // k is known: the pair is over
+            if (stop) {
+                pair_stop(D, gc, stop);
+                return true;
+            }
             epoch++;
             if (*(volatile uint32_t *)&gc->susp[epoch & 1]) {
                 // save round t - 1 of the band for the next launch, then leave
@@ -1750,6 +1800,9 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         S.jd->jid = 0;
         S.jd->slot = -1;
         *S.jring = 0;
+        for (int i = 0; i < JOB_RING; i++)
+            reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 120)[i] = 0;
+        *reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 128) = 0;
         for (int i = 0; S.stg && i < P.stage; i++) {
             const Stage T = stage_of(S.stg + i * STAGE_STRIDE);
             mbar_init(T.bar, 1);

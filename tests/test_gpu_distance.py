@@ -205,9 +205,11 @@ def test_lcp_length_workload_reduced(ctxs, orc, p0):
 
 def test_skew_lengthens_the_slides(ctxs):
     """Fig. 4's x axis: the mean LCP per diagonal-extension grows with the
-    skew of the two symbols."""
+    skew of the two symbols.  (Between P(0) = 0.5 and 0.9 the exact mean
+    differs by a few per cent only, about what CTAs that run blocks past k
+    add to the device's count; 0.99 and 0.999 are well apart.)"""
     means = []
-    for p0 in (0.5, 0.9, 0.99):
+    for p0 in (0.5, 0.99, 0.999):
         p = W.lcp_length_pair(1000, p0, n=200_000)
         ctxs["default"].distance_dev(dev(p.A), dev(p.B))
         st = ctxs["default"].stats()
