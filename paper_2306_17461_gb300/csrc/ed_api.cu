@@ -1119,30 +1119,39 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
     cudaStream_t s = (cudaStream_t)stream;
     int r;
     if (method == 2 || method == 7) {
-        if ((r = ensure(ctx, ctx->slots, sizeof(JobSlot) * q)) != ED_OK)
+        // one job per query (job id 1, pair 0 of a one-entry pair table)
+        if (n >= (1ull << 31) || m >= (1ull << 31))
+            return ED_EINVAL;
+        if ((r = ensure(ctx, ctx->slots, sizeof(JobSlot) * q)) != ED_OK ||
+            (r = ensure(ctx, ctx->pdesc, sizeof(PairDesc))) != ED_OK)
             return r;
+        PairDesc pd{};
+        pd.A = A;
+        pd.B = B;
+        pd.n = (int64_t)n;
+        pd.m = (int64_t)m;
+        CK(cudaMemcpyAsync(ctx->pdesc.p, &pd, sizeof(pd), cudaMemcpyHostToDevice, s));
+        const unsigned long long tg = 1ull << 32;
         std::vector<JobSlot> it(q);
+        std::vector<int64_t> lim(q);
         for (size_t i = 0; i < q; i++) {
             JobSlot &j = it[i];
             j = JobSlot{};
-            j.x = x[i];
-            j.y = y[i];
-            j.lim = std::min<int64_t>((int64_t)n - x[i], (int64_t)m - y[i]);
-            j.result = (unsigned long long)j.lim;
-            j.nchunks = (unsigned)((j.lim + CHUNK_BYTES - 1) / CHUNK_BYTES);
-            j.claim = 1ull << 32;
-            j.A = A;
-            j.B = B;
-            j.n = (long long)n;
-            j.m = (long long)m;
+            lim[i] = std::min<int64_t>((int64_t)n - x[i], (int64_t)m - y[i]);
+            j.xt = tg | (uint32_t)x[i];
+            j.yt = tg | (uint32_t)y[i];
+            j.lt = tg | (uint32_t)lim[i];
+            j.pt = tg;
+            j.result = tg | (uint32_t)~(uint32_t)lim[i];
+            j.claim = tg;
         }
         CK(cudaMemcpyAsync(ctx->slots.p, it.data(), sizeof(JobSlot) * q, cudaMemcpyHostToDevice, s));
         CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, nullptr, nullptr, (int64_t)q, method, nullptr,
-                              nullptr, (JobSlot *)ctx->slots.p, ctx->grid, s));
+                              nullptr, (JobSlot *)ctx->slots.p, (const PairDesc *)ctx->pdesc.p, ctx->grid, s));
         CK(cudaMemcpyAsync(it.data(), ctx->slots.p, sizeof(JobSlot) * q, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         for (size_t i = 0; i < q; i++)
-            out[i] = (int64_t)it[i].result;
+            out[i] = std::min<int64_t>(lim[i], (int64_t)(uint32_t)~(uint32_t)it[i].result);
         return ED_OK;
     }
     if ((r = ensure(ctx, ctx->qx, 8 * q)) != ED_OK || (r = ensure(ctx, ctx->qy, 8 * q)) != ED_OK ||
@@ -1158,7 +1167,7 @@ int ed_lcp_dev(ed_ctx *ctx, const uint8_t *A, size_t n, const uint8_t *B, size_t
     std::memcpy(H.pow2, ctx->pow2, sizeof(H.pow2));
     CK(launch_lcp_queries(A, (int64_t)n, B, (int64_t)m, (const int64_t *)ctx->qx.p, (const int64_t *)ctx->qy.p,
                           (int64_t)q, method >= 5 ? method - 2 : method, &H, (int64_t *)ctx->qo.p, nullptr,
-                          ctx->grid, s));
+                          nullptr, ctx->grid, s));
     CK(cudaMemcpyAsync(out, ctx->qo.p, 8 * q, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     return ED_OK;

@@ -24,22 +24,19 @@ constexpr unsigned long long DONE_STOPPED = ~0ull - 1;
 // A long slide open for help.  Each CTA owns JOB_RING slots, used in turn.
 // `claim` packs the job id (high 32 bits) and the count of claims made (low
 // 32 bits): every atomicAdd of 1 claims the next chunk (CHUNK_BYTES of each
-// string), and the owner closes the job by adding a high bit to the count
-// (the protocol is in lv_tiles.cu); `result` (first mismatch offset, starts
-// at lim) falls by atomicMin; `bits` marks the chunks scanned; `done` counts
-// answered claims (a slot is reused once it covers every claim).
+// string).  The descriptor words (x, y, lim, the pair's index in the
+// launch's pair table), the result (~ the least mismatch offset) and one
+// answer word per chunk each carry a job id in their high half; answers are
+// raised by red.max (the protocol is in lv_tiles.cu).
 constexpr int JOB_RING = 2;
 constexpr int JOB_MAX_CHUNKS = 4096; // chunks of one job; longer slides are cut
 struct __align__(128) JobSlot {
     unsigned long long claim;
+    unsigned long long pad0[15]; // the claim word alone in its 128-byte line
+    unsigned long long xt, yt, lt, pt;
     unsigned long long result;
-    long long x, y, lim;
-    unsigned int done, nchunks;
-    const uint8_t *A, *B; // the strings compared (any pair of the launch)
-    long long n, m;
-    unsigned int nvalid;  // claims made before the close (the owner's record)
-    unsigned int pad;
-    unsigned long long bits[JOB_MAX_CHUNKS / 64];
+    unsigned long long pad1[11];
+    unsigned long long ans[JOB_MAX_CHUNKS];
 };
 
 // One pair of a tile launch.
@@ -195,8 +192,8 @@ struct HashArgs {
 // slots[i].result; the others use x, y, out.
 cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
                                const int64_t *x, const int64_t *y, int64_t q, int method,
-                               const HashArgs *hash, int64_t *out, JobSlot *slots, int grid,
-                               cudaStream_t s);
+                               const HashArgs *hash, int64_t *out, JobSlot *slots, const PairDesc *pairs,
+                               int grid, cudaStream_t s);
 
 // ---------------------------------------------------------------- hash
 // stride 1: T[i] = h(X[0..i)) for i = 0..len; stride b > 1: T[j] = h(X[0..jb))

@@ -44,7 +44,6 @@
 namespace edg {
 
 constexpr int64_t GROW_NUM = 9, GROW_DEN = 8; // epoch radius growth factor
-constexpr uint32_t CLAIM_CLOSE = 1u << 31; // set in the claim count by the owner
 // Polls of the edge words by warp 0 before the CTA looks at anything else.
 constexpr int HALO_SPINS = 4;
 // Looks at the job slots by thread 0 of a CTA without a tile before its
@@ -54,6 +53,7 @@ constexpr int IDLE_SPINS = 32;
 // and how long the claim count may stand still before the owner scans a
 // chunk itself.
 constexpr int WATCH_SPINS = 8;
+constexpr int WATCH_WORDS = 4; // answer words a lane loads per look
 constexpr uint64_t OWN_SCAN_NS = 1000;
 
 struct Counters {
@@ -154,6 +154,7 @@ __device__ __noinline__ int64_t hash_lcp(const uint64_t *pow2, const HashView VA
 struct Pair {
     const uint8_t *A, *B;
     int64_t n, m;
+    int32_t q; // its index in the launch's pair table (job descriptors name it)
     const uint64_t *TA, *TB;
     bool hash;
 };
@@ -277,70 +278,82 @@ struct Smem {
     unsigned long long *diag;
 };
 
-// Job slot protocol.  claim = (job id << 32) | count.  Every atomicAdd of 1
-// is one claim of chunk `count` (CHUNK_BYTES of each string); a claim whose
-// count has CLAIM_CLOSE set arrived after the owner closed the job and is
-// void.  Each valid claim is answered by exactly one increment of `done`
-// (after scanning the chunk, or at once when the chunk lies past the end or
-// past the best mismatch).  A claim that lands on a job published after the
-// claimer looked is still a valid claim of that job: the descriptor read
-// after the atomic (and a fence) is that job's, because the slot cannot be
-// republished before `done` covers it.
-__device__ __forceinline__ bool claim_valid(unsigned long long w)
+// Job slot protocol.  claim = (job id << 32) | count: every atomicAdd of 1
+// claims chunk `count` (CHUNK_BYTES of each string) of the job the word
+// names.  The job's descriptor words and every word a claimer writes back
+// carry a job id in their high half: job ids grow with every job of a slot,
+// and the answers are raised by red.max, so an answer of a job the slot no
+// longer holds (from a claimer that fell behind) never overwrites one of the
+// job it holds.  A slot is therefore reused with no wait for the claims of
+// its last job, and nothing is cleared.  A claim that lands on a job
+// published after the claimer looked is a claim of that job (the descriptor
+// read after the atomic, and a fence, carries its id).
+//   ans[c]  = (jid << 32) | job offset of the chunk's first mismatch (NOMIS: none)
+//   result  = (jid << 32) | ~best  (so that red.max keeps the least offset)
+constexpr uint32_t NOMIS = 0xffffffffu;
+
+__device__ __forceinline__ bool claim_valid(unsigned long long w) { return (w >> 32) != 0; }
+
+__device__ __forceinline__ void red_max_u64(unsigned long long *p, unsigned long long v)
 {
-    return (w >> 32) != 0 && !((uint32_t)w & CLAIM_CLOSE);
+    asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Answers one valid claim of chunk c: marks the chunk answered and counts
-// the answer.  A chunk with a mismatch lowers the result first and marks
-// itself with release order, so that a reader that sees the mark (acquire)
-// sees the lowered result; a chunk without one wrote nothing else, and its
-// mark and count need no order and do not make the thread wait.  (A slot is
-// reused only once every mark and count of its claims is seen.)
-__device__ __forceinline__ void answer_claim(JobSlot *sl, int64_t c, int64_t r)
+// The least mismatch offset of job jid in the result word w (lim: none
+// reported, or the word is another job's).
+__device__ __forceinline__ int64_t result_of(unsigned long long w, uint32_t jid, int64_t lim)
 {
-    const bool mark = c >= 0 && c < JOB_MAX_CHUNKS;
-    unsigned long long *bw = &sl->bits[mark ? c >> 6 : 0];
-    const unsigned long long bit = 1ull << (c & 63);
-    if (r >= 0) {
-        atomicMin(&sl->result, (unsigned long long)r);
-        if (mark)
-            asm volatile("red.release.gpu.global.or.b64 [%0], %1;" ::"l"(bw), "l"(bit) : "memory");
-    } else if (mark) {
-        asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(bw), "l"(bit) : "memory");
-    }
-    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&sl->done) : "memory");
+    return (uint32_t)(w >> 32) == jid ? min(lim, (int64_t)(uint32_t)~(uint32_t)w) : lim;
 }
 
-// Thread 0, after a valid claim w of slot s: whether its chunk is still
-// worth scanning (inside lim and below the best mismatch found so far).
-// The job's descriptor is read into the CTA's cache once per job (the claim
-// word names the job), after a fence that orders it behind the claim.  For
-// the job already cached no fence is needed: the claim is valid, so the job
-// was open when the claim landed, and any earlier read of its result was
-// this job's (at worst too high, which only costs a scan).  A descriptor
-// outside its strings is never scanned (self-check record 7).
-__device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsigned long long w,
+// Answers claim c of job jid: a mismatch at job offset r lowers the result,
+// and the chunk's word records the answer (no order needed between them: the
+// owner decides from the chunk words alone).
+__device__ __forceinline__ void answer_claim(JobSlot *sl, uint32_t jid, int64_t c, int64_t r)
+{
+    const unsigned long long tg = (unsigned long long)jid << 32;
+    if (r >= 0)
+        red_max_u64(&sl->result, tg | (uint32_t)~(uint32_t)r);
+    if (c >= 0 && c < JOB_MAX_CHUNKS)
+        red_max_u64(&sl->ans[c], tg | (r >= 0 ? (uint32_t)r : NOMIS));
+}
+
+// Thread 0, after a claim w of slot s: whether its chunk is worth scanning
+// (inside lim and below the best mismatch reported so far).  The job's
+// descriptor is read into the CTA's cache once per job, after a fence that
+// orders it behind the claim: x, y, lim and the pair (whose strings the
+// launch's pair table holds), each word tagged with its job; words of
+// another job mean the slot has moved on (the claim's job is over: nothing
+// to scan).  best: the result word read along with the claim (~0: read it
+// here).  A descriptor outside its strings is never scanned (self-check
+// record 7).
+__device__ __forceinline__ int claim_go(const LvArgs &P, const Smem S, JobSlot *sl, int s, unsigned long long w,
                                         unsigned long long best = ~0ull)
 {
     const uint32_t jid = (uint32_t)(w >> 32);
     const int64_t c = (int64_t)(uint32_t)w;
     JobDesc *J = S.jd;
-    bool fresh = false;
     if (J->jid != jid || J->slot != s) {
-        fresh = true;
         __threadfence();
-        // the slot is rewritten for every job: read it past the L1
-        J->A = (const uint8_t *)__ldcg((const unsigned long long *)&sl->A);
-        J->B = (const uint8_t *)__ldcg((const unsigned long long *)&sl->B);
-        J->n = __ldcg(&sl->n);
-        J->m = __ldcg(&sl->m);
-        J->x = __ldcg(&sl->x);
-        J->y = __ldcg(&sl->y);
-        J->lim = __ldcg(&sl->lim);
+        const unsigned long long xt = ld_relaxed_u64(&sl->xt), yt = ld_relaxed_u64(&sl->yt);
+        const unsigned long long lt = ld_relaxed_u64(&sl->lt), pt = ld_relaxed_u64(&sl->pt);
+        best = ld_relaxed_u64(&sl->result);
+        if ((uint32_t)(xt >> 32) != jid || (uint32_t)(yt >> 32) != jid || (uint32_t)(lt >> 32) != jid ||
+            (uint32_t)(pt >> 32) != jid) {
+            J->jid = 0;
+            return 0;
+        }
+        const PairDesc &D = P.pairs[(uint32_t)pt];
+        J->A = D.A;
+        J->B = D.B;
+        J->n = D.n;
+        J->m = D.m;
+        J->x = (uint32_t)xt;
+        J->y = (uint32_t)yt;
+        J->lim = (uint32_t)lt;
         J->jid = jid;
         J->slot = s;
-        if (J->x < 0 || J->y < 0 || J->lim < 0 || J->x + J->lim > J->n || J->y + J->lim > J->m || !J->A || !J->B) {
+        if (J->x + J->lim > J->n || J->y + J->lim > J->m || !J->A || !J->B) {
             J->jid = 0;
             if (S.err && atomicCAS(S.err, 0u, 7u) == 0u) {
                 S.diag[0] = 7;
@@ -353,14 +366,11 @@ __device__ __forceinline__ int claim_go(const Smem S, JobSlot *sl, int s, unsign
             }
             return 0;
         }
+    } else if (best == ~0ull) {
+        best = ld_relaxed_u64(&sl->result);
     }
-    // best: read along with the claim (any read made while one of this CTA's
-    // claims on the job was unanswered is this job's); for a job just read
-    // in, after the fence
-    if (fresh || best == ~0ull)
-        best = *(volatile unsigned long long *)&sl->result;
     const int64_t cs = c * (int64_t)CHUNK_BYTES;
-    return (cs < J->lim && (unsigned long long)cs < best) ? 1 : 0;
+    return cs < result_of(best, jid, J->lim) ? 1 : 0;
 }
 
 // The first mismatch of A[x0..x0+len) vs B[y0..) (len <= CHUNK_BYTES), or
@@ -377,9 +387,10 @@ __device__ __forceinline__ int64_t chunk_scan(const LvArgs &P, const Smem S, con
     return sweep_scan<CHUNK_BYTES / (CTA_THREADS * 16)>(A, n, B, m, x0, y0, len, S.smin);
 }
 
-// The whole CTA scans claimed chunk c of the job cached in S.jd (when go)
+// The whole CTA scans claimed chunk c of job jid, cached in S.jd (when go),
 // and answers the claim.
-__device__ __forceinline__ void scan_claim(const LvArgs &P, const Smem S, JobSlot *sl, int64_t c, int go)
+__device__ __forceinline__ void scan_claim(const LvArgs &P, const Smem S, JobSlot *sl, uint32_t jid, int64_t c,
+                                           int go)
 {
     int64_t r = -1;
     if (go) {
@@ -390,7 +401,7 @@ __device__ __forceinline__ void scan_claim(const LvArgs &P, const Smem S, JobSlo
         r = q >= 0 ? cs + q : -1;
     }
     if (threadIdx.x == 0)
-        answer_claim(sl, c, r);
+        answer_claim(sl, jid, c, r);
 }
 
 // What ends a CTA's helping early: the first edge word of both neighbours
@@ -428,25 +439,25 @@ __device__ int claim_loop(const LvArgs &P, const Smem S, JobSlot *sl, int s, uns
         if (tid == 0) {
             const bool ready = wake && wake_ready(wake);
             const int valid = claim_valid(w) ? 1 : 0;
-            const int go = valid ? claim_go(S, sl, s, w, best) : 0;
+            const int go = valid ? claim_go(P, S, sl, s, w, best) : 0;
             S.bc[0] = valid;
             S.bc[3] = go;
-            S.bcl[0] = (int64_t)(uint32_t)w;
+            S.bcl[0] = (long long)w;
             // the next claim and a look at the result, both in flight during
             // the scan below (this claim is still unanswered: the job cannot
             // change meanwhile)
             const bool next = go && !ready && made + 1 < budget;
             w = next ? atomicAdd(&sl->claim, 1ull) : 0ull;
-            best = next ? *(volatile unsigned long long *)&sl->result : ~0ull;
+            best = next ? ld_relaxed_u64(&sl->result) : ~0ull;
             S.bc[4] = next;
         }
         __syncthreads();
         const int valid = S.bc[0], go = S.bc[3], more = S.bc[4];
-        const int64_t c = S.bcl[0];
+        const unsigned long long wc = (unsigned long long)S.bcl[0];
         __syncthreads();
         if (!valid)
             break;
-        scan_claim(P, S, sl, c, go);
+        scan_claim(P, S, sl, (uint32_t)(wc >> 32), (int64_t)(uint32_t)wc, go);
         made++;
         if (!more)
             break;
@@ -469,17 +480,18 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
     int made = 0, ps = 1;        // ps: the stage holding the pending chunk
     int pvalid = 0, pgo = 0;     // the pending claim (staged last turn)
     int64_t pc = 0;
+    uint32_t pjid = 0;
     for (;;) {
         const int sn = ps ^ 1;   // the stage for the claim resolved this turn
         if (tid == 0) {
             // 1. the claim in flight: valid, worth a scan?
             const int nv = wn && claim_valid(wn) ? 1 : 0;
-            const int ng = nv ? claim_go(S, sl, s, wn, bestn) : 0;
-            const int64_t nc = (int64_t)(uint32_t)wn;
+            const int ng = nv ? claim_go(P, S, sl, s, wn, bestn) : 0;
+            const unsigned long long wc = wn;
             // 2. its copies, in flight while the pending chunk is compared
             if (ng) {
                 const JobDesc &J = *S.jd;
-                const int64_t cs = nc * (int64_t)CHUNK_BYTES;
+                const int64_t cs = (int64_t)(uint32_t)wc * (int64_t)CHUNK_BYTES;
                 stage_issue(sn ? T1 : T0, J.A, J.n, J.B, J.m, J.x + cs, J.y + cs,
                             min((int64_t)CHUNK_BYTES, (int64_t)J.lim - cs), true);
             }
@@ -487,14 +499,15 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
             const bool ready = wake && wake_ready(wake);
             const bool more = ng && !ready && made + pvalid + nv < budget;
             wn = more ? atomicAdd(&sl->claim, 1ull) : 0ull;
-            bestn = more ? *(volatile unsigned long long *)&sl->result : ~0ull;
+            bestn = more ? ld_relaxed_u64(&sl->result) : ~0ull;
             S.bc[0] = nv;
             S.bc[3] = ng;
-            S.bcl[0] = nc;
+            S.bcl[0] = (long long)wc;
         }
         __syncthreads();
         const int nv = S.bc[0], ng = S.bc[3];
-        const int64_t nc = S.bcl[0];
+        const unsigned long long wcn = (unsigned long long)S.bcl[0];
+        const int64_t nc = (int64_t)(uint32_t)wcn;
         __syncthreads();
         // 4. the pending chunk: compared (when worth it) and answered
         if (pvalid) {
@@ -511,13 +524,14 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
                 }
             }
             if (tid == 0)
-                answer_claim(sl, pc, r);
+                answer_claim(sl, pjid, pc, r);
             made++;
         }
         // 5. the claim resolved this turn is the pending one now
         pvalid = nv;
         pgo = ng;
         pc = nc;
+        pjid = (uint32_t)(wcn >> 32);
         ps = sn;
         if (!pvalid)
             break;
@@ -569,25 +583,15 @@ __device__ __forceinline__ bool serve_slot(const LvArgs &P, const Smem S, int s,
     return claim_loop(P, S, &P.slots[s], s, 0ull, budget, wake) > 0;
 }
 
-// Whether mark word w (chunks 64w .. 64w+63) marks every chunk below need.
-__device__ __forceinline__ bool marks_cover(unsigned long long mw, uint32_t w, uint32_t need)
-{
-    if (w * 64 >= need)
-        return true;
-    const uint32_t hi = min(need - w * 64, 64u);
-    const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
-    return (mw & want) == want;
-}
-
 // One job of the CTA's long slide (whole CTA): the first mismatch of
 // A[x..x+lim) vs B[y..), lim <= JOB_MAX_CHUNKS chunks, or lim.  The job goes
-// into the CTA's next ring slot (once every claim of the job that slot held
-// before is answered), its chunk 0 claimed by the CTA itself; the chunks are
-// claimed in order by the CTA and by every CTA that is waiting on a
-// neighbour or has no tile.  The CTA watches the job: its answer is final
-// once every chunk up to the one holding the best mismatch (or every chunk)
-// is marked answered; the CTA then closes the job and returns without
-// waiting for claims past that chunk.
+// into the CTA's next ring slot (no wait: see the protocol above), its
+// chunk 0 claimed by the CTA itself; the other chunks are claimed in order by
+// the CTA and by every CTA that is waiting on a neighbour or has no tile.
+// The CTA watches the chunks' answer words: the job is done once every chunk
+// before the first one with a mismatch (or every chunk) has answered.  It
+// then takes its bit out of the active mask and returns; claims that come
+// later find their chunk past the result and answer at once.
 __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pair Q, int64_t x, int64_t y,
                                         int64_t lim)
 {
@@ -598,60 +602,17 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
     JobSlot *sl = &P.slots[sidx];
     const int word = sidx >> 6;
     const unsigned long long bit = 1ull << (sidx & 63);
-    // ------------------------------------------------ reuse of the slot
-    // (skipped when the CTA's previous job already checked it and cleared its
-    // marks: prep[ring])
-    int *prep = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 120);
-    const bool ready = prep[ring] != 0;
-    if (tid < 32 && !ready) {
-        // every claim of the slot's last job answered, and its marks seen
-        // (the claims made before its close; 0 for a slot not used yet)
-        const uint32_t cnt = sl->nvalid;
-        const uint32_t need = min(cnt, (uint32_t)JOB_MAX_CHUNKS);
-        const uint64_t t0 = gtimer();
-        for (;;) {
-            bool ok = true;
-            for (uint32_t w = lane; w * 64 < need; w += 32) {
-                const uint32_t hi = min(need - w * 64, 64u);
-                const unsigned long long want = hi == 64 ? ~0ull : ((1ull << hi) - 1ull);
-                ok &= ((*(volatile unsigned long long *)&sl->bits[w]) & want) == want;
-            }
-            ok = __all_sync(0xffffffffu, ok);
-            ok = ok && *(volatile unsigned int *)&sl->done >= cnt;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (ok)
-                break;
-            if (gtimer() - t0 > P.spin_ns) {
-                if (lane == 0)
-                    wait_failed(P, 6, 0, cnt, *(volatile unsigned int *)&sl->done, sidx, 0);
-                break;
-            }
-        }
-    }
-    // warp 0 clears the marks the job will use (each lane fenced before the
-    // barrier, so that the release below orders them before the job opens)
-    if (tid < 32 && !ready) {
-        for (uint32_t w = tid; w * 64 < nch; w += 32)
-            sl->bits[w] = 0ull;
-        __threadfence();
-    }
-    __syncthreads();
     // ------------------------------------------------ publish
     if (tid == 0) {
-        prep[ring] = 0;
         *S.jring = (ring + 1) % JOB_RING;
-        sl->A = Q.A;
-        sl->B = Q.B;
-        sl->n = Q.n;
-        sl->m = Q.m;
-        sl->x = x;
-        sl->y = y;
-        sl->lim = lim;
-        sl->result = (unsigned long long)lim;
-        sl->done = 0;
-        sl->nchunks = nch;
-        uint32_t jid = (uint32_t)(sl->claim >> 32) + 1u;
+        uint32_t jid = (uint32_t)(ld_relaxed_u64(&sl->claim) >> 32) + 1u;
         jid = jid ? jid : 1u;
+        const unsigned long long tg = (unsigned long long)jid << 32;
+        sl->xt = tg | (uint32_t)x;
+        sl->yt = tg | (uint32_t)y;
+        sl->lt = tg | (uint32_t)lim;
+        sl->pt = tg | (uint32_t)Q.q;
+        sl->result = tg | (uint32_t)~(uint32_t)lim;
         // the CTA's own cache holds the job: no read back
         JobDesc *J = S.jd;
         J->A = Q.A;
@@ -663,99 +624,97 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
         J->lim = lim;
         J->jid = jid;
         J->slot = sidx;
-        // count 1: chunk 0 is the CTA's own claim; the descriptor and the
-        // cleared marks are visible before the claim word (release), which
-        // opens the job
-        st_release_u64(&sl->claim, ((unsigned long long)jid << 32) | 1ull);
-        asm volatile("red.relaxed.gpu.global.or.b64 [%0], %1;" ::"l"(&P.ctl->active[word]), "l"(bit) : "memory");
-        S.bcl[2] = (long long)((unsigned long long)jid << 32);
+        // count 1: chunk 0 is the CTA's own claim; the descriptor is visible
+        // before the claim word (release), which opens the job, and before
+        // the active bit (release)
+        st_release_u64(&sl->claim, tg | 1ull);
+        asm volatile("red.release.gpu.global.or.b64 [%0], %1;" ::"l"(&P.ctl->active[word]), "l"(bit) : "memory");
+        S.bcl[2] = (long long)tg;
     }
     __syncthreads();
     const unsigned long long w0 = (unsigned long long)S.bcl[2];
+    const uint32_t jid = (uint32_t)(w0 >> 32);
     __syncthreads();
-    claim_loop(P, S, sl, sidx, w0, 1, nullptr, (unsigned long long)lim); // chunk 0 (no mismatch known yet)
+    claim_loop(P, S, sl, sidx, w0, 1, nullptr, w0 | (uint32_t)~(uint32_t)lim); // chunk 0
     // ------------------------------------------------ watch
-    // warp 0 looks at the result, the claim count and the marks together
-    // (several looks before the CTA meets at a barrier): final once every
-    // chunk up to the one holding the best mismatch is marked answered, the
-    // result then read again after an acquire fence (every mismatch of a
-    // chunk seen answered is in it).  With no claim by another CTA for
-    // OWN_SCAN_NS (no helper at hand), the CTA scans a chunk itself.
-    static_assert(JOB_MAX_CHUNKS <= 64 * 64, "two mark words per lane");
-    uint32_t last = 1;
-    uint64_t tnew = gtimer(); // lane 0: when the claim count last moved
-    bool first = true;        // warp 1: the other slot still to prepare
+    // warp 0 loads the answer words of the next WATCH_WORDS * 32 chunks from
+    // `base` on (every chunk below base has answered without a mismatch),
+    // several looks before the CTA meets at a barrier.  With no progress for
+    // OWN_SCAN_NS (no helper at hand), the CTA claims a chunk itself, or scans
+    // the claimed chunk at base again itself.
+    uint32_t base = 0, last = 1;
+    uint64_t tnew = gtimer(); // lane 0: when the job last moved
     for (;;) {
         if (tid < 32) {
-            int act = 0; // 0 look again, 1 scan a chunk, 2 final
+            int act = 0; // 0 look again, 1 claim a chunk, 2 final, 3 scan chunk base itself
             unsigned long long best = 0;
             for (int spin = 0; spin < WATCH_SPINS && act == 0; spin++) {
-                const unsigned long long best0 = *(volatile unsigned long long *)&sl->result;
-                const uint32_t cnt = (uint32_t)*(volatile unsigned long long *)&sl->claim & ~CLAIM_CLOSE;
-                const uint32_t w0 = (uint32_t)lane, w1 = (uint32_t)lane + 32;
-                const unsigned long long m0 = w0 * 64 < nch ? *(volatile unsigned long long *)&sl->bits[w0] : 0ull;
-                const unsigned long long m1 = w1 * 64 < nch ? *(volatile unsigned long long *)&sl->bits[w1] : 0ull;
-                const uint32_t cs = best0 < (unsigned long long)lim ? (uint32_t)(best0 / CHUNK_BYTES) : nch - 1;
-                const uint32_t need = min(cs + 1, nch);
-                const bool ok = __all_sync(0xffffffffu, marks_cover(m0, w0, need) && marks_cover(m1, w1, need));
-                if (ok) {
-                    fence_acquire();
-                    if (lane == 0)
-                        best = *(volatile unsigned long long *)&sl->result;
-                    act = 2;
-                } else if (lane == 0) {
-                    const uint64_t now = gtimer();
-                    if (cnt != last) {
-                        last = cnt;
-                        tnew = now;
-                    } else if (cnt < nch && now - tnew > OWN_SCAN_NS) {
-                        act = 1;
-                        last = cnt + 1; // the CTA's own claim
+                const uint32_t cnt = (uint32_t)ld_relaxed_u64(&sl->claim);
+                unsigned long long v[WATCH_WORDS];
+#pragma unroll
+                for (int i = 0; i < WATCH_WORDS; i++) {
+                    const uint32_t c = base + 32u * (uint32_t)i + (uint32_t)lane;
+                    v[i] = c < nch ? ld_relaxed_u64(&sl->ans[c]) : (w0 | NOMIS);
+                }
+                uint32_t nb = base;
+#pragma unroll
+                for (int i = 0; i < WATCH_WORDS; i++) {
+                    if (act != 0 || nb != base + 32u * (uint32_t)i)
+                        break;
+                    const bool a = (uint32_t)(v[i] >> 32) == jid;
+                    const bool mis = a && (uint32_t)v[i] != NOMIS;
+                    const unsigned int A = __ballot_sync(0xffffffffu, a), M = __ballot_sync(0xffffffffu, mis);
+                    const int fu = ~A ? __ffs((int)~A) - 1 : 32; // first unanswered
+                    const int fm = M ? __ffs((int)M) - 1 : 32;   // first mismatch
+                    if (fm < fu) {
+                        best = __shfl_sync(0xffffffffu, (uint32_t)v[i], fm);
+                        act = 2;
+                    } else if (fu < 32) {
+                        nb += (uint32_t)fu;
+                    } else {
+                        nb += 32;
+                        if (nb >= nch) {
+                            best = (unsigned long long)lim;
+                            act = 2;
+                        }
                     }
                 }
+                if (act == 0 && lane == 0) {
+                    const uint64_t now = gtimer();
+                    if (nb != base || cnt != last) {
+                        last = cnt;
+                        tnew = now;
+                    } else if (now - tnew > OWN_SCAN_NS) {
+                        // the chunk at base: claimed and slow (scan it again
+                        // here), or not claimed yet (claim it)
+                        act = nb < cnt ? 3 : 1;
+                        tnew = now;
+                    }
+                }
+                base = nb;
                 act = __shfl_sync(0xffffffffu, act, 0);
             }
             if (lane == 0) {
                 S.bc[5] = act;
                 S.bcl[1] = (long long)best;
-            }
-        } else if (tid < 64 && first) {
-            // warp 1, once: the CTA's other slot (its next job's) -- every
-            // claim of the job it held answered and marked -- gets its marks
-            // cleared now, off the next job's path
-            first = false;
-            const int o = (ring + 1) % JOB_RING;
-            JobSlot *so = &P.slots[(int)blockIdx.x * JOB_RING + o];
-            const uint32_t cnt = so->nvalid;
-            const uint32_t need = min(cnt, (uint32_t)JOB_MAX_CHUNKS);
-            bool ok = true;
-            for (uint32_t w = lane; w * 64 < need; w += 32)
-                ok &= marks_cover(*(volatile unsigned long long *)&so->bits[w], w, need);
-            ok = __all_sync(0xffffffffu, ok) && *(volatile unsigned int *)&so->done >= cnt;
-            if (ok) {
-                for (uint32_t w = lane; w < JOB_MAX_CHUNKS / 64; w += 32)
-                    so->bits[w] = 0ull;
-                __threadfence();
-                __syncwarp();
-                if (lane == 0)
-                    prep[o] = 1;
+                S.bc[6] = (int)base;
             }
         }
         __syncthreads();
         const int act = S.bc[5];
         const int64_t best = S.bcl[1];
+        const int64_t cb = S.bc[6];
         __syncthreads();
         if (act == 2) {
-            if (tid == 0) {
+            if (tid == 0)
                 asm volatile("red.relaxed.gpu.global.and.b64 [%0], %1;" ::"l"(&P.ctl->active[word]), "l"(~bit)
                              : "memory");
-                // claims after the close are void (never answered, never marked)
-                sl->nvalid = (uint32_t)atomicAdd(&sl->claim, (unsigned long long)CLAIM_CLOSE);
-            }
             return best;
         }
         if (act == 1)
             claim_loop(P, S, sl, sidx, 0ull, 1);
+        if (act == 3)
+            scan_claim(P, S, sl, jid, cb, 1);
     }
 }
 
@@ -878,7 +837,7 @@ __device__ Smem carve(const LvArgs &P)
     S.nR = S.nL + 7;
     S.jd = reinterpret_cast<JobDesc *>(p + 192);
     S.jring = reinterpret_cast<int *>(p + 48);
-    // p + 168 .. p + 176: prep[JOB_RING] (run_job); p + 176: lone (lean_slides)
+    // p + 176: lone (lean_slides)
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -1428,7 +1387,7 @@ __device__ void pair_stop(const PairDesc &D, GroupCtl *gc, uint32_t status)
 
 // Runs one pair on the group; kc is the radius its re-tiling buffers hold.
 // Returns false if the launch must stop.
-__device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const PairDesc &D, GroupCtl *gc, int gi, int G,
+__device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const PairDesc &D, int q, GroupCtl *gc, int gi, int G,
                          int c0, int32_t *gfb, int64_t kc, uint64_t deadline,
                          Counters &C)
 {
@@ -1441,6 +1400,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
     Q.m = D.m;
     Q.TA = D.TA;
     Q.TB = D.TB;
+    Q.q = q;
     Q.hash = P.use_hash && D.TA && D.TB;
     const int64_t n = Q.n, m = Q.m, nm = max(n, m);
     const int64_t gstride = 2 * kc + 5;
@@ -1800,8 +1760,6 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         S.jd->jid = 0;
         S.jd->slot = -1;
         *S.jring = 0;
-        for (int i = 0; i < JOB_RING; i++)
-            reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 120)[i] = 0;
         *reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 128) = 0;
         for (int i = 0; S.stg && i < P.stage; i++) {
             const Stage T = stage_of(S.stg + i * STAGE_STRIDE);
@@ -1853,7 +1811,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
         if (q < 0)
             break;
         const PairDesc D = P.pairs[q];
-        const bool ok = run_pair(P, S, D, gc, gi, G, c0, gfb, kc, deadline, C);
+        const bool ok = run_pair(P, S, D, q, gc, gi, G, c0, gfb, kc, deadline, C);
         flush_counters(D, C, gi == 0);
         if (!ok)
             break;
@@ -1925,7 +1883,8 @@ __global__ void lcp_query_kernel(const uint8_t *A, int64_t n, const uint8_t *B, 
 // answers stay in the slots.
 __device__ uint32_t g_lcp_grid_err; // status word of the test launches below
 
-__global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots, int stage)
+__global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, int nslots, int stage,
+                                                                const PairDesc *pairs)
 {
     extern __shared__ __align__(128) unsigned char gsm[];
     __shared__ unsigned long long s_min;
@@ -1941,6 +1900,7 @@ __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, i
     S.stg = stage ? gsm : nullptr;
     LvArgs P{};
     P.spin_ns = 2000000000ull;
+    P.pairs = pairs;
     if (threadIdx.x == 0) {
         s_jd.jid = 0;
         s_jd.slot = -1;
@@ -1961,8 +1921,8 @@ __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, i
 
 cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, int64_t m,
                                const int64_t *x, const int64_t *y, int64_t q, int method,
-                               const HashArgs *hash, int64_t *out, JobSlot *slots, int grid,
-                               cudaStream_t s)
+                               const HashArgs *hash, int64_t *out, JobSlot *slots, const PairDesc *pairs,
+                               int grid, cudaStream_t s)
 {
     if (q == 0)
         return cudaSuccess;
@@ -1976,7 +1936,7 @@ cudaError_t launch_lcp_queries(const uint8_t *A, int64_t n, const uint8_t *B, in
             if (e != cudaSuccess)
                 return e;
         }
-        lcp_grid_kernel<<<grid, CTA_THREADS, smem, s>>>(slots, (int)q, stage);
+        lcp_grid_kernel<<<grid, CTA_THREADS, smem, s>>>(slots, (int)q, stage, pairs);
         return cudaGetLastError();
     }
     HashArgs H{};

@@ -24,9 +24,8 @@ def test_cache_matches_generators_and_bounds(name):
         assert n == ns[i]
         assert e <= ks[i]
         assert abs(n - m) <= k <= e
-    # the file is complete for the batch set (the served set is written last)
-    if name == "batch":
-        assert len(cache) == npairs
+    # both files are complete
+    assert len(cache) == npairs
 
 
 @pytest.mark.parametrize("name", ["batch", "serve"])
