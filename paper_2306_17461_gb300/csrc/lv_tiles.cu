@@ -233,9 +233,10 @@ __device__ __noinline__ void wait_failed(const LvArgs &P, unsigned long long sit
 // A helper CTA's copy of the job it claims from (read once per job).
 struct JobDesc {
     const uint8_t *A, *B;
-    long long n, m, x, y, lim;
+    int32_t n, m, x, y, lim; // (strings of the tile kernel are shorter than 2^31)
     uint32_t jid;
     int32_t slot;
+    int32_t pq; // the pair whose strings A, B are (-1: none yet)
 };
 static_assert(sizeof(JobDesc) <= 64, "the job cache fills bytes 192..255 of the smem header");
 
@@ -328,32 +329,54 @@ __device__ __forceinline__ void answer_claim(JobSlot *sl, uint32_t jid, int64_t 
 // here).  A descriptor outside its strings is never scanned (self-check
 // record 7).
 __device__ __forceinline__ int claim_go(const LvArgs &P, const Smem S, JobSlot *sl, int s, unsigned long long w,
-                                        unsigned long long best = ~0ull)
+                                        unsigned long long best = ~0ull, const unsigned long long *pre = nullptr)
 {
     const uint32_t jid = (uint32_t)(w >> 32);
     const int64_t c = (int64_t)(uint32_t)w;
     JobDesc *J = S.jd;
     if (J->jid != jid || J->slot != s) {
-        __threadfence();
-        const unsigned long long xt = ld_relaxed_u64(&sl->xt), yt = ld_relaxed_u64(&sl->yt);
-        const unsigned long long lt = ld_relaxed_u64(&sl->lt), pt = ld_relaxed_u64(&sl->pt);
-        best = ld_relaxed_u64(&sl->result);
-        if ((uint32_t)(xt >> 32) != jid || (uint32_t)(yt >> 32) != jid || (uint32_t)(lt >> 32) != jid ||
-            (uint32_t)(pt >> 32) != jid) {
-            J->jid = 0;
-            return 0;
+        // the words read along with the claim serve when they all carry its
+        // job (each word holds its tag with its value); else read them again
+        // behind a fence
+        unsigned long long xt = 0, yt = 0, lt = 0, pt = 0;
+        bool tags = false;
+        if (pre) {
+            xt = pre[0];
+            yt = pre[1];
+            lt = pre[2];
+            pt = pre[3];
+            tags = (uint32_t)(xt >> 32) == jid && (uint32_t)(yt >> 32) == jid && (uint32_t)(lt >> 32) == jid &&
+                   (uint32_t)(pt >> 32) == jid;
         }
-        const PairDesc &D = P.pairs[(uint32_t)pt];
-        J->A = D.A;
-        J->B = D.B;
-        J->n = D.n;
-        J->m = D.m;
-        J->x = (uint32_t)xt;
-        J->y = (uint32_t)yt;
-        J->lim = (uint32_t)lt;
+        if (!tags) {
+            __threadfence();
+            xt = ld_relaxed_u64(&sl->xt);
+            yt = ld_relaxed_u64(&sl->yt);
+            lt = ld_relaxed_u64(&sl->lt);
+            pt = ld_relaxed_u64(&sl->pt);
+            best = ld_relaxed_u64(&sl->result);
+            if ((uint32_t)(xt >> 32) != jid || (uint32_t)(yt >> 32) != jid || (uint32_t)(lt >> 32) != jid ||
+                (uint32_t)(pt >> 32) != jid) {
+                J->jid = 0;
+                return 0;
+            }
+        }
+        // the pair's strings: the launch's pair table, read once per pair
+        if (J->pq != (int32_t)(uint32_t)pt) {
+            const PairDesc &D = P.pairs[(uint32_t)pt];
+            J->A = D.A;
+            J->B = D.B;
+            J->n = (int32_t)D.n;
+            J->m = (int32_t)D.m;
+            J->pq = (int32_t)(uint32_t)pt;
+        }
+        J->x = (int32_t)(uint32_t)xt;
+        J->y = (int32_t)(uint32_t)yt;
+        J->lim = (int32_t)(uint32_t)lt;
         J->jid = jid;
         J->slot = s;
-        if (J->x + J->lim > J->n || J->y + J->lim > J->m || !J->A || !J->B) {
+        if (J->x < 0 || J->y < 0 || J->lim < 0 || (int64_t)J->x + J->lim > J->n || (int64_t)J->y + J->lim > J->m ||
+            !J->A || !J->B) {
             J->jid = 0;
             if (S.err && atomicCAS(S.err, 0u, 7u) == 0u) {
                 S.diag[0] = 7;
@@ -475,8 +498,15 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
     const int tid = threadIdx.x;
     const Stage T0 = stage_of(S.stg), T1 = stage_of(S.stg + STAGE_STRIDE);
     unsigned long long wn = 0, bestn = ~0ull; // thread 0: the claim in flight, the result read with it
-    if (tid == 0)
+    unsigned long long pre[4] = {0, 0, 0, 0};  // thread 0: the descriptor words read with the first claim
+    if (tid == 0) {
         wn = atomicAdd(&sl->claim, 1ull);
+        pre[0] = ld_relaxed_u64(&sl->xt);
+        pre[1] = ld_relaxed_u64(&sl->yt);
+        pre[2] = ld_relaxed_u64(&sl->lt);
+        pre[3] = ld_relaxed_u64(&sl->pt);
+        bestn = ld_relaxed_u64(&sl->result);
+    }
     int made = 0, ps = 1;        // ps: the stage holding the pending chunk
     int pvalid = 0, pgo = 0;     // the pending claim (staged last turn)
     int64_t pc = 0;
@@ -486,7 +516,7 @@ __device__ int claim_loop2(const LvArgs &P, const Smem S, JobSlot *sl, int s, in
         if (tid == 0) {
             // 1. the claim in flight: valid, worth a scan?
             const int nv = wn && claim_valid(wn) ? 1 : 0;
-            const int ng = nv ? claim_go(P, S, sl, s, wn, bestn) : 0;
+            const int ng = nv ? claim_go(P, S, sl, s, wn, bestn, made + pvalid == 0 ? pre : nullptr) : 0;
             const unsigned long long wc = wn;
             // 2. its copies, in flight while the pending chunk is compared
             if (ng) {
@@ -617,11 +647,12 @@ __device__ __noinline__ int64_t run_job(const LvArgs &P, const Smem S, const Pai
         JobDesc *J = S.jd;
         J->A = Q.A;
         J->B = Q.B;
-        J->n = Q.n;
-        J->m = Q.m;
-        J->x = x;
-        J->y = y;
-        J->lim = lim;
+        J->n = (int32_t)Q.n;
+        J->m = (int32_t)Q.m;
+        J->pq = Q.q;
+        J->x = (int32_t)x;
+        J->y = (int32_t)y;
+        J->lim = (int32_t)lim;
         J->jid = jid;
         J->slot = sidx;
         // count 1: chunk 0 is the CTA's own claim; the descriptor is visible
@@ -1759,6 +1790,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
     if (threadIdx.x == 0) { // no job cached (read before the first group barrier)
         S.jd->jid = 0;
         S.jd->slot = -1;
+        S.jd->pq = -1;
         *S.jring = 0;
         *reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(S.jring) + 128) = 0;
         for (int i = 0; S.stg && i < P.stage; i++) {
@@ -1904,6 +1936,7 @@ __global__ void __launch_bounds__(CTA_THREADS) lcp_grid_kernel(JobSlot *slots, i
     if (threadIdx.x == 0) {
         s_jd.jid = 0;
         s_jd.slot = -1;
+        s_jd.pq = -1;
         if (stage) {
             const Stage T = stage_of(gsm);
             mbar_init(T.bar, 1);
