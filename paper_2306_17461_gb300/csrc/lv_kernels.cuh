@@ -65,7 +65,10 @@ struct __align__(64) GroupCtl {
     int32_t pair;              // pair index being run (-1: none left)
     uint32_t ebar_count, ebar_gen; // epoch-change barrier (abandoned once k is known)
     uint32_t susp[2];          // epoch e ends the launch's share of the pair: susp[e & 1]
-    uint32_t pad[5];
+    uint32_t pad;
+    // the furthest row of the band and its diagonal at epoch e's change:
+    // lead[e & 1] = max over tiles of (L << 32) | (d + 2^31)
+    unsigned long long lead[2];
 };
 
 // Per launch (zeroed before the launch).

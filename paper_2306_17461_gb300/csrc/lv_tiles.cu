@@ -868,7 +868,7 @@ __device__ Smem carve(const LvArgs &P)
     S.nR = S.nL + 7;
     S.jd = reinterpret_cast<JobDesc *>(p + 192);
     S.jring = reinterpret_cast<int *>(p + 48);
-    // p + 176: lone (lean_slides)
+    // p + 176: lone (lean_slides); p + 184: the tile's lead at an epoch change
     p += 256;
     S.lcap = P.smax + 2 * HMAX + 2;
     S.ld = reinterpret_cast<int32_t *>(p);
@@ -904,8 +904,12 @@ struct Tile {
 // diagonals per CTA).
 constexpr int64_t HELP_BAND = 256;
 
+// The tiles' grid is shifted so that diagonal dp (the band's furthest row:
+// the alignment path) lies in the middle of its tile, when the one more tile
+// this may take is at hand: the path's long slides then run in one tile only,
+// not also in its neighbour's halo.
 __device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int gi, int c0, int h, int help_div,
-                                          int64_t smax)
+                                          int64_t smax, int64_t dp)
 {
     Tile T;
     T.lo_all = max(-R, -Q.n);
@@ -918,10 +922,16 @@ __device__ __forceinline__ Tile partition(const Pair &Q, int64_t R, int G, int g
             Gt = g2;
     }
     T.S = max((int64_t)h, (N + Gt - 1) / Gt);
-    T.ntiles = (int)((N + T.S - 1) / T.S);
+    int64_t sh = 0;
+    if (dp >= T.lo_all && dp <= T.hi_all) {
+        sh = ((T.S / 2 - (dp - T.lo_all)) % T.S + T.S) % T.S;
+        if ((N + sh + T.S - 1) / T.S > G)
+            sh = 0;
+    }
+    T.ntiles = (int)((N + sh + T.S - 1) / T.S);
     T.has = gi < T.ntiles;
-    T.a = T.lo_all + (int64_t)gi * T.S;
-    T.b = min(T.hi_all + 1, T.a + T.S);
+    T.a = max(T.lo_all, T.lo_all + (int64_t)gi * T.S - sh);
+    T.b = min(T.hi_all + 1, T.lo_all + (int64_t)(gi + 1) * T.S - sh);
     T.left = (T.has && gi > 0) ? c0 + gi - 1 : -1;
     T.right = (T.has && gi + 1 < T.ntiles) ? c0 + gi + 1 : -1;
     return T;
@@ -1448,7 +1458,7 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         R = D.R0;
     }
     uint32_t epoch = 0;
-    Tile T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax);
+    Tile T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax, 0);
     if (T.S > P.smax || (D.keep && R > D.keep_r)) {
         pair_stop(D, gc, ST_WIDE);
         if (tid == 0 && gi == 0 && t > 0) { // the saved state is still good
@@ -1579,11 +1589,26 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 }
             }
             int32_t *buf = gfb + ((epoch + 1) & 1) * gstride;
+            unsigned long long *lead_s = reinterpret_cast<unsigned long long *>(
+                reinterpret_cast<unsigned char *>(S.jring) + 136);
+            if (tid == 0)
+                *lead_s = 0ull;
+            __syncthreads();
             if (T.has) {
                 const int32_t *src = frontier(S, t - 1);
-                for (int64_t d = T.a + tid; d < T.b; d += nt)
-                    st_cg(buf + d + kc + 2, src[d - (T.a - h) + 1]);
+                unsigned long long lm = 0ull; // the tile's furthest row and its diagonal
+                for (int64_t d = T.a + tid; d < T.b; d += nt) {
+                    const int32_t v = src[d - (T.a - h) + 1];
+                    st_cg(buf + d + kc + 2, v);
+                    if (v >= 0)
+                        lm = max(lm, ((unsigned long long)(uint32_t)v << 32) | (uint32_t)(d + 0x80000000ll));
+                }
+                if (lm)
+                    atomicMax(lead_s, lm);
             }
+            __syncthreads();
+            if (tid == 0 && *lead_s)
+                atomicMax(&gc->lead[(epoch + 1) & 1], *lead_s);
             if (leader) {
                 // the leader alone decides whether the launch leaves the pair here
                 gc->susp[(epoch + 1) & 1] = (wide || (can_suspend && gtimer() >= deadline)) ? 1u : 0u;
@@ -1616,7 +1641,14 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             }
             t_ep = t;
             R = Rn;
-            T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax);
+            // the band's lead (read by every CTA after the barrier: the same
+            // tiles everywhere); the other word is free again for the next
+            // change once every CTA has passed this barrier
+            const unsigned long long lead = *(volatile unsigned long long *)&gc->lead[epoch & 1];
+            if (leader)
+                gc->lead[(epoch + 1) & 1] = 0ull;
+            T = partition(Q, R, G, gi, c0, h, P.help_div, P.smax,
+                          lead ? (int64_t)(uint32_t)lead - 0x80000000ll : 0);
             if (T.S > P.smax) {
                 pair_stop(D, gc, ST_WIDE);
                 return true;
@@ -1834,6 +1866,7 @@ __global__ void __launch_bounds__(CTA_THREADS, 1) lv_tiles_kernel(LvArgs P)
             gc->done_k = ~0ull;
             gc->epoch_req = 0;
             gc->epoch_t = 0;
+            gc->lead[0] = gc->lead[1] = 0ull;
             gc->ebar_count = 0; // no CTA is inside the epoch barrier here
             __threadfence();
         }
