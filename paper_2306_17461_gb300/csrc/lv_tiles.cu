@@ -1779,8 +1779,10 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
             if (st == 3)
                 break;
             if (js >= 0) {
+                // two claims at most (one pipeline fill): a tile's own next
+                // block waits on the chunks it has in flight
                 const Wake wk{lw, rw, tag};
-                serve_slot(P, S, js, 16, &wk);
+                serve_slot(P, S, js, 2, &wk);
             }
         }
         C.tm[2] += clock64() - tw0;
