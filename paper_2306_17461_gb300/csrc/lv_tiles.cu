@@ -444,8 +444,8 @@ __device__ __forceinline__ bool wake_ready(const Wake *w)
 // The whole CTA claims and scans chunks of slot s's job, in order, up to
 // `budget` claims: thread 0 makes the next claim before the current chunk
 // is scanned, so that its round trip overlaps the scan.  w0: a claim made
-// already (0: make the first one here).  Stops at a void claim, once a
-// claimed chunk lies past the end or past the best mismatch (that claim is
+// already (0: make the first one here).  Stops once a claimed chunk lies
+// past the end or past the best mismatch, or its job is over (that claim is
 // answered at once), or, with a Wake, once the CTA's neighbours are ready
 // (checked along with each claim).  Returns the number of claims made and
 // answered.
