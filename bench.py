@@ -737,7 +737,7 @@ def main():
     ap.add_argument("--hash-block", type=int, default=0, help="block size b of --lcp bhash (0: 32)")
     ap.add_argument("--ks", default=DEFAULT_KS)
     ap.add_argument("--skews", default="0.5,0.9,0.99,0.999,0.9999")
-    ap.add_argument("--block-rounds", type=int, default=0, help="rounds per temporal block (0: 16)")
+    ap.add_argument("--block-rounds", type=int, default=0, help="rounds per temporal block (0: 32)")
     ap.add_argument("--n", type=int, default=0)
     ap.add_argument("--npairs", type=int, default=4096)
     ap.add_argument("--npairs-serve", type=int, default=512)

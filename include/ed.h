@@ -68,8 +68,8 @@ typedef struct {
     int tile_width;           /* diagonals per CTA in the first epoch (the
                                  tiles grow with the band, by an eighth at
                                  a time); 0 = 64 */
-    int block_rounds;         /* rounds between neighbour exchanges (1..16);
-                                 0 = 16 */
+    int block_rounds;         /* rounds between neighbour exchanges (1..64);
+                                 0 = 32 */
     int64_t max_rounds;       /* frontier capacity in rounds; 0 = the larger
                                  string length (at most 2^28) */
     int hash_block;           /* block size b of ED_LCP_BHASH (1..4096);

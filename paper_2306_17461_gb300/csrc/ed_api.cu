@@ -160,7 +160,7 @@ struct TileOut {
 struct Eff {
     int lcp_mode = ED_LCP_DIRECT; // AUTO resolved
     int hash_block = 32;
-    int block_rounds = HMAX;
+    int block_rounds = 32;
     int tile_width = 64;
     int warp_cap = 4096;
     int local_chunks = 0;

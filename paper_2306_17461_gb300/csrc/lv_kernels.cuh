@@ -14,7 +14,7 @@ constexpr uint32_t ST_SUSPENDED = 9; // per pair: budget spent, frontier saved t
 
 constexpr int CTA_THREADS = 256;   // threads of a tile CTA (up to 255 registers each)
 constexpr int MAX_GRID = 1024;     // CTAs of one tile launch, at most
-constexpr int HMAX = 16;           // rounds per temporal block, at most
+constexpr int HMAX = 64;           // rounds per temporal block, at most
 constexpr int CHUNK_BYTES = 16 * 1024; // bytes of one job-slot claim (per string)
 constexpr int SMAX_LIMIT = 16384;  // widest tile a CTA keeps in shared memory
 constexpr int MAX_CLS = 12;        // group-size classes of one tile launch

@@ -1728,7 +1728,8 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
         const unsigned long long *lw = T.left >= 0 ? halo_ptr(P, T.left, parity, 1) : nullptr;
         const unsigned long long *rw = T.right >= 0 ? halo_ptr(P, T.right, parity, 0) : nullptr;
         // wait for both neighbours' words (warp 0: lanes 0..15 the left
-        // neighbour's, 16..31 the right one's), helping open slides meanwhile
+        // neighbour's, 16..31 the right one's; lane j reads words j, j + 16,
+        // j + 32 and j + 48 of its side), helping open slides meanwhile
         const uint64_t t0 = tid == 0 ? gtimer() : 0;
         for (;;) {
             if (tid < 32) {
@@ -1736,12 +1737,25 @@ __device__ __forceinline__ bool run_pair(const LvArgs &P, const Smem S, const Pa
                 const unsigned long long *wp = side ? rw : lw;
                 int st = 0, js = -1;
                 for (int spin = 0; spin < HALO_SPINS; spin++) {
-                    const unsigned long long v = (j < h && wp) ? ld_relaxed_u64(wp + j) : ~0ull;
+                    unsigned long long v[HMAX / 16];
+                    bool ok = true;
+#pragma unroll
+                    for (int u = 0; u < HMAX / 16; u++) {
+                        const int jj = j + 16 * u;
+                        v[u] = (jj < h && wp) ? ld_relaxed_u64(wp + jj) : ~0ull;
+                    }
                     // an open job of another CTA, looked for in the same round trip
                     int q = tid == 0 ? pick_slot(P) : -1;
-                    if (__all_sync(0xffffffffu, (uint32_t)(v >> 32) >= tag)) {
-                        if (j < h)
-                            edge[(side ? b + j : a - h + j) - off] = wp ? (int32_t)(uint32_t)v : NEG;
+#pragma unroll
+                    for (int u = 0; u < HMAX / 16; u++)
+                        ok = ok && (uint32_t)(v[u] >> 32) >= tag;
+                    if (__all_sync(0xffffffffu, ok)) {
+#pragma unroll
+                        for (int u = 0; u < HMAX / 16; u++) {
+                            const int jj = j + 16 * u;
+                            if (jj < h)
+                                edge[(side ? b + jj : a - h + jj) - off] = wp ? (int32_t)(uint32_t)v[u] : NEG;
+                        }
                         st = 3;
                         break;
                     }

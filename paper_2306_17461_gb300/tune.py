@@ -5,7 +5,9 @@ For each workload class -- the longer string's length n and the edit rate
 k / n, on seeded synthetic pairs shaped like the paper's workloads (Sec. 6:
 random strings with k planted insertions, deletions and substitutions) --
 the sweep starts from the built-in defaults and, one parameter at a time,
-keeps the value with the lowest median device time (coordinate descent):
+keeps the value with the lowest median device time (coordinate descent,
+repeated until a pass changes nothing, --passes at most; a setting is
+measured once):
 
     block_rounds  rounds between neighbour exchanges
     tile_width    diagonals per CTA in the first epoch
@@ -21,7 +23,7 @@ this module: tune_sweep.tsv (every measurement) and tune_table.tsv (one row
 per class, the format ed_tune_lookup reads; classes without a measurement
 take the nearest measured rate of their length).
 
-    python -m paper_2306_17461_gb300.tune [--reps 3] [--quick]
+    python -m paper_2306_17461_gb300.tune [--reps 3] [--passes 3] [--quick]
 """
 from __future__ import annotations
 
@@ -38,10 +40,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # class edges: length buckets and edit-rate buckets of the table
 N_EDGES = [0, 3e6, 3e7, 3e8, 1e12]
 R_EDGES = [0, 3e-6, 3e-5, 3e-4, 1.0]
-DEFAULTS = {"lcp_mode": 1, "block_rounds": 16, "tile_width": 64, "warp_cap": 4096, "local_chunks": -1,
+DEFAULTS = {"lcp_mode": 1, "block_rounds": 32, "tile_width": 64, "warp_cap": 4096, "local_chunks": -1,
             "help_div": 8}
 CANDIDATES = {
-    "block_rounds": [4, 8, 16],
+    "block_rounds": [8, 16, 32, 64],
     "tile_width": [16, 64, 256],
     "warp_cap": [2048, 4096, 16384],
     "local_chunks": [-1, 2, 8, 32],
@@ -85,7 +87,7 @@ def measure(ed, dA, dB, params, reps):
         ctx.close()
 
 
-def sweep(reps: int, quick: bool, log=print):
+def sweep(reps: int, quick: bool, passes: int = 3, log=print):
     import torch
 
     from paper_2306_17461_gb300 import binding as ed
@@ -100,20 +102,26 @@ def sweep(reps: int, quick: bool, log=print):
         t_def, k_ref = measure(ed, dA, dB, cur, reps)
         rows.append((name, n, k_ref, dict(cur), t_def))
         t_best = t_def
-        for key, values in CANDIDATES.items():
-            for v in values:
-                if v == cur[key]:
-                    continue
-                # the hash searches cost seconds at k = 1e5: measured below that
-                if key == "lcp_mode" and k_planted > 20_000:
-                    continue
-                trial = dict(cur, **{key: v})
-                t, k = measure(ed, dA, dB, trial, reps)
-                if k != k_ref:
-                    raise RuntimeError(f"{name}: distance {k} with {trial}, {k_ref} with the defaults")
-                rows.append((name, n, k, trial, t))
-                if t < t_best:
-                    t_best, cur = t, trial
+        seen = {tuple(sorted(cur.items()))}
+        for _ in range(passes):
+            start = dict(cur)
+            for key, values in CANDIDATES.items():
+                for v in values:
+                    # the hash searches cost seconds at k = 1e5: measured below that
+                    if key == "lcp_mode" and k_planted > 20_000:
+                        continue
+                    trial = dict(cur, **{key: v})
+                    if tuple(sorted(trial.items())) in seen:
+                        continue
+                    seen.add(tuple(sorted(trial.items())))
+                    t, k = measure(ed, dA, dB, trial, reps)
+                    if k != k_ref:
+                        raise RuntimeError(f"{name}: distance {k} with {trial}, {k_ref} with the defaults")
+                    rows.append((name, n, k, trial, t))
+                    if t < t_best:
+                        t_best, cur = t, trial
+            if cur == start:
+                break
         log(f"{name}: k={k_ref} default {t_def:.3f} ms, best {t_best:.3f} ms with {cur}")
         best_by_class[(n, k_ref / n)] = (cur, t_def, t_best)
         del dA, dB
@@ -165,6 +173,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--quick", action="store_true", help="n <= 1e7 only")
+    ap.add_argument("--passes", type=int, default=3, help="coordinate-descent passes at most")
     a = ap.parse_args()
     import sys
 
@@ -175,7 +184,7 @@ def main():
 
     binding.load()
     dev = torch.cuda.get_device_name(0)
-    rows, best = sweep(a.reps, a.quick)
+    rows, best = sweep(a.reps, a.quick, a.passes)
     write(rows, best, f"{dev}, {time.strftime('%Y-%m-%d')}")
 
 

@@ -11,12 +11,16 @@ from paper_2306_17461_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# kernel configurations exercised: default; narrow first tiles (many epoch
-# changes, the band crosses many tiles); one round per block; odd block
-# lengths and few CTAs; one CTA; the hash LCP on full and on blocked prefix
-# tables (Sec. 3.3; blocks of 32 and of 7 characters)
+# kernel configurations exercised: default (32 rounds per block); 16 and
+# 64 rounds per block (the largest), the latter with tiles as narrow as
+# allowed; narrow first tiles (many epoch changes, the band crosses many
+# tiles); one round per block; odd block lengths and few CTAs; one CTA; the
+# hash LCP on full and on blocked prefix tables (Sec. 3.3; blocks of 32 and
+# of 7 characters)
 CONFIGS = {
     "default": {},
+    "h16": {"block_rounds": 16},
+    "h64_narrow": {"block_rounds": 64, "tile_width": 1},
     "wide": {"tile_width": 1, "block_rounds": 4},
     "wide_g3": {"tile_width": 2, "grid_ctas": 3, "block_rounds": 3},
     "h1": {"block_rounds": 1, "tile_width": 1},
