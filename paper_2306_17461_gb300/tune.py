@@ -87,6 +87,37 @@ def measure(ed, dA, dB, params, reps):
         ctx.close()
 
 
+def descend(cost, start, candidates, passes, skip=lambda key, v: False):
+    """Coordinate descent from `start`: one parameter of `candidates` at a
+    time, the value with the lowest cost(setting)[0] is kept.  Passes repeat
+    until one changes nothing (`passes` at most); every setting is measured
+    once; skip(key, value) leaves a value out.  Returns the best setting, its
+    cost and every (setting, cost, extra) measured, the start's first."""
+    cur = dict(start)
+    t0, x0 = cost(cur)
+    measured = [(dict(cur), t0, x0)]
+    best = t0
+    seen = {tuple(sorted(cur.items()))}
+    for _ in range(passes):
+        before = dict(cur)
+        for key, values in candidates.items():
+            for v in values:
+                if skip(key, v):
+                    continue
+                trial = dict(cur, **{key: v})
+                sig = tuple(sorted(trial.items()))
+                if sig in seen:
+                    continue
+                seen.add(sig)
+                t, x = cost(trial)
+                measured.append((trial, t, x))
+                if t < best:
+                    best, cur = t, trial
+        if cur == before:
+            break
+    return cur, best, measured
+
+
 def sweep(reps: int, quick: bool, passes: int = 3, log=print):
     import torch
 
@@ -98,30 +129,19 @@ def sweep(reps: int, quick: bool, passes: int = 3, log=print):
         p = make()
         dA = torch.from_numpy(p.A).cuda()
         dB = torch.from_numpy(p.B).cuda()
-        cur = dict(DEFAULTS)
-        t_def, k_ref = measure(ed, dA, dB, cur, reps)
-        rows.append((name, n, k_ref, dict(cur), t_def))
-        t_best = t_def
-        seen = {tuple(sorted(cur.items()))}
-        for _ in range(passes):
-            start = dict(cur)
-            for key, values in CANDIDATES.items():
-                for v in values:
-                    # the hash searches cost seconds at k = 1e5: measured below that
-                    if key == "lcp_mode" and k_planted > 20_000:
-                        continue
-                    trial = dict(cur, **{key: v})
-                    if tuple(sorted(trial.items())) in seen:
-                        continue
-                    seen.add(tuple(sorted(trial.items())))
-                    t, k = measure(ed, dA, dB, trial, reps)
-                    if k != k_ref:
-                        raise RuntimeError(f"{name}: distance {k} with {trial}, {k_ref} with the defaults")
-                    rows.append((name, n, k, trial, t))
-                    if t < t_best:
-                        t_best, cur = t, trial
-            if cur == start:
-                break
+        ref = {}
+
+        def cost(params):
+            t, k = measure(ed, dA, dB, params, reps)
+            if ref.setdefault("k", k) != k:
+                raise RuntimeError(f"{name}: distance {k} with {params}, {ref['k']} with the defaults")
+            return t, k
+
+        # the hash searches cost seconds at k = 1e5: measured below that
+        cur, t_best, measured = descend(cost, DEFAULTS, CANDIDATES, passes,
+                                        skip=lambda key, v: key == "lcp_mode" and k_planted > 20_000)
+        k_ref, t_def = ref["k"], measured[0][1]
+        rows += [(name, n, k, params, t) for params, t, k in measured]
         log(f"{name}: k={k_ref} default {t_def:.3f} ms, best {t_best:.3f} ms with {cur}")
         best_by_class[(n, k_ref / n)] = (cur, t_def, t_best)
         del dA, dB
